@@ -1,0 +1,273 @@
+"""Benchmark: Sternheimer solves/s and chi0bar applications/s at 1e-8 residual on one GB300.
+
+Workload (the medium configuration): cubic cell L = 20 bohr, FFT grid 64^3, plane-wave cutoff
+|G|^2 <= 25 bohr^-2 (16,879 plane waves, 8,440 stored at Gamma), 32 Gaussian-well atoms with s and
+p Kleinman-Bylander projectors (128 projectors), 64 occupied orbitals (computed by the library),
+128 orthonormal seeded perturbations. One step is one pass of the whole hot path over that block:
+wdf_pdep_davidson with one iteration, i.e. v^1/2, dV in real space, right-hand sides, the
+64 x 128 = 8,192 Sternheimer solves to ||b - A x|| <= 1e-8 ||b||, the density response, v^1/2 and
+the Rayleigh-Ritz step of PDEP (subspace matrix, FP64 eigensolve, Ritz residuals).
+
+Timing: W warm-up steps, then K steps bracketed by barriers and device synchronisation, CUDA events
+on the library's stream; L2 is flushed (256 MiB write) before every step and the step's working
+set (~10 GB) exceeds L2 anyway. The e2e figure repeats the step through the same C ABI with host
+buffers (host-to-device copy of the perturbations and device-to-host copy of the eigenpairs
+inside the timed region). Multi-GPU: the path shards by perturbation blocks with no exchange, so
+each rank runs its own block (weak scaling) and rank 0 reports the total.
+
+--impl reference times the FP64 CPU oracle instead (a bounded sample of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "medium"
+NPERT = 128
+NEIG = 64
+METRIC = "sternheimer_solves_per_s_at_1e-8"
+UNIT = "solves/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("bf16_tflops", 1862.0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(system_name: str, nsolve_target: int = 64):
+    """Time the FP64 oracle on one perturbation (all occupied orbitals) of the workload."""
+    from oracle import dfpt, hamiltonian
+
+    s = synth.make_system(system_name)
+    H = hamiltonian.Hamiltonian(s)
+    t0 = time.time()
+    w, psi = H.ground_state(s.nocc, tol=1e-6)
+    t_gs = time.time() - t0
+    R = dfpt.Response(H, w, psi)
+    phi = synth.make_perturbations(s, 1, 0)
+    return s, R, phi, t_gs
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on a bounded sample, one perturbation per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s, R, phi, t_gs = oracle_sample(WORKLOAD)
+    times = []
+    nsolve = s.nocc
+    for i in range(args.warmup + args.steps):
+        t0 = time.time()
+        o = R.apply(phi, tol=1e-8)
+        dt = time.time() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = nsolve / (ms * 1e-3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "medium: L=20 bohr, 64^3 grid, 25 bohr^-2 cutoff, 32 atoms, 64 occupied, 1 perturbation per step",
+                   "cg_tol": 1e-8},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle",
+                         "sample": f"1 perturbation x {nsolve} occupied orbitals = {nsolve} Sternheimer solves per step (FP64 numpy/scipy oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cg_iters_per_solve": float(np.mean(o["iters"])),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_14025_gb300 import build as wbuild
+    from paper_2607_14025_gb300 import wdf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        wbuild.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    s = synth.make_system(WORKLOAD)
+    # each rank applies chi0bar to its own seeded perturbation block (weak scaling)
+    phi_h = synth.make_perturbations(s, NPERT, 1000 + rank)
+    ctx = wdf.Context(s, precision=args.precision, cg_tol=1e-8, stream=stream.cuda_stream, device=local,
+                      max_batch=args.max_batch)
+    gap = None
+    eps, _ = ctx.orbitals()
+    phi_d = torch.from_numpy(phi_h).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(phi):
+        try:
+            return ctx.pdep(NEIG, phi, maxiter=1, tol=1e-8)
+        except wdf.NotConverged as e:  # one Davidson iteration never converges all 64 pairs
+            return e.result
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step(phi_d)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clk = Clocks(local)
+        clk.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stats = []
+        for i in range(args.steps):
+            flush.fill_(1.0)
+            ev[i][0].record(stream)
+            lam, vec, st = step(phi_d)
+            ev[i][1].record(stream)
+            stats.append(st.as_dict())
+        torch.cuda.synchronize(dev)
+        clocks = clk.stop()
+        ms_dev = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        # end to end through the C ABI with host buffers
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            lam_h, vec_h, st_h = step(phi_h)
+        torch.cuda.synchronize(dev)
+        ms_e2e = 1e3 * (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_dev, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_dev, ms_e2e = float(t[0]), float(t[1])
+    nsolve = stats[-1]["nsolve"]
+    iters = stats[-1]["cg_iters"] / max(1, nsolve)
+    value = world * nsolve / (ms_dev * 1e-3)
+    e2e = world * nsolve / (ms_e2e * 1e-3)
+    ctx.close()
+    if rank != 0:
+        return
+    hbm, bf16, src = peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": "medium: L=20 bohr, 64^3 grid, |G|^2<=25, 8440 stored PWs, 32 atoms (128 KB projectors), "
+                               "64 occupied, 128 perturbations per GPU, PDEP 64 eigenpairs, one Davidson iteration per step",
+                   "precision": args.precision, "cg_tol": 1e-8, "l2": "flushed (256 MiB write) before each step; working set > L2",
+                   "parallelism": f"perturbation blocks x{world}"},
+        "chi0_applies_per_s": world * NPERT / (ms_dev * 1e-3),
+        "cg_iters_per_solve": iters,
+        "max_residual": stats[-1]["max_residual"],
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,
+                "d2h_bytes_per_step": NEIG * s.npw_h * 16 + NEIG * 8},
+        "gpu_launches": None,
+        "clocks": clocks,
+        "peaks_source": src,
+    }
+    if args.cpu_baseline:
+        sys_o, R, phi1, t_gs = oracle_sample(WORKLOAD)
+        t0 = time.time()
+        o = R.apply(phi1, tol=1e-8)
+        dt = time.time() - t0
+        line["cpu_baseline"] = {"value": sys_o.nocc / dt, "unit": UNIT, "cores": cores(), "kind": "oracle",
+                                "sample": f"1 perturbation x {sys_o.nocc} occupied = {sys_o.nocc} Sternheimer solves at 1e-8 "
+                                          f"(ground state by the oracle's iterative eigensolver, {t_gs:.0f} s, not timed)"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["wdf", "reference"], default="wdf")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--max-batch", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * wdf.h -- C ABI of the GB300 DFPT screening library (libwdf.so).
+ *
+ * The library applies the symmetrised independent-particle response
+ *     chi0bar = v^1/2 chi0 v^1/2
+ * to blocks of plane-wave perturbations by density-functional perturbation theory, and finds the
+ * lowest eigenpairs of chi0bar by block Davidson (projective dielectric eigendecomposition,
+ * PDEP). Paper: "The WEST code for large-scale excited-state materials simulations", Sec. 2.1
+ * (W_p = v^1/2 chibar v^1/2; chibar from the PDEP eigenpairs of chi0bar, Eq. (5); the density
+ * response from Sternheimer equations without empty states) and Sec. 3.3 (one Davidson solver).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: hartree atomic units (energies in hartree, lengths in bohr).
+ * Plane waves: orthonormal b_G(r) = Omega^-1/2 exp(iG.r), Gamma point, real functions, so only
+ *   the half sphere is stored: npw_h Miller triples with G = 0 first and, for every other G in
+ *   the list, -G absent from it. A half-sphere vector is npw_h complex numbers stored as
+ *   interleaved doubles (re, im), 2*npw_h doubles; a block of n vectors is n consecutive vectors.
+ *   Inner product of two such vectors: a0 b0 + 2 Re sum_{G != 0} conj(a_G) b_G.
+ * Real-space grids: n1*n2*n3 doubles, index i1 + n1*(i2 + n2*i3) for the point
+ *   r = (i1/n1) a1 + (i2/n2) a2 + (i3/n3) a3.
+ * Memory: arguments documented as "host or device" are read from host memory when the call's
+ *   mem argument is WDF_MEM_HOST and from device memory of the context's GPU when it is
+ *   WDF_MEM_DEVICE. Other pointers are always host memory. The library copies what it needs,
+ *   never frees caller memory and keeps no caller pointer after a call returns.
+ * Streams: all GPU work of a context runs on the stream given at setup (0: the legacy default
+ *   stream). Calls return after their results are in the caller's buffer unless stated.
+ * Errors: every int-returning call returns WDF_OK (0) or one of the codes below and never aborts
+ *   the process; the GPU never traps. wdf_last_error() gives a message for the last failure.
+ *   A CUDA failure inside a context marks it failed (WDF_ESTATE on later calls) until destroyed.
+ */
+#ifndef WDF_H
+#define WDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum wdf_status {
+  WDF_OK = 0,
+  WDF_EINVAL = 1,   /* invalid argument or descriptor */
+  WDF_ENOMEM = 2,   /* device or host allocation failed */
+  WDF_ECUDA = 3,    /* CUDA runtime error (message in wdf_last_error) */
+  WDF_ENOCONV = 4,  /* an iteration hit its limit; outputs hold the last iterate, stats filled */
+  WDF_ETIMEOUT = 5, /* reserved: a bounded device-side wait expired */
+  WDF_ENAN = 6,     /* non-finite value in an input or an iterate */
+  WDF_ESTATE = 7    /* context unusable after an earlier CUDA failure, or no GPU */
+};
+
+enum wdf_mem { WDF_MEM_HOST = 0, WDF_MEM_DEVICE = 1 };
+
+/* Arithmetic of the Sternheimer solves.
+ * WDF_FP64: every FFT, product, projection and CG update in FP64.
+ * WDF_MIXED: inner conjugate-gradient iterations in FP32 (FFTs, H application, projections);
+ *   the residual b - A x, the accumulated solution, the density response and the Davidson linear
+ *   algebra in FP64 (iterative refinement), so the stopping test is an FP64 residual. */
+enum wdf_precision { WDF_FP64 = 0, WDF_MIXED = 1 };
+
+enum wdf_precond { WDF_PRECOND_NONE = 0, WDF_PRECOND_TPA = 1 };
+
+typedef struct wdf_ctx wdf_ctx;
+
+/* The model system. Paper Sec. 2.1, Eq. (1): H psi_i = eps_i psi_i with
+ * H = -1/2 nabla^2 + V_loc(r) + sum_j |beta_j> D_j <beta_j| (local plus Kleinman-Bylander). */
+typedef struct wdf_system {
+  double cell[9];        /* lattice vectors a1, a2, a3 as rows (bohr); host */
+  int n[3];              /* FFT grid n1, n2, n3; each a product of 2, 3, 5, at most 128 (FP64: 96) */
+  int npw_h;             /* number of half-sphere plane waves */
+  const int32_t *miller; /* [npw_h][3] Miller indices (host); G = 0 first; for each (n1, n2)
+                            column the n3 values must form one interval over the full sphere */
+  const double *vloc_r;  /* [n3][n2][n1] local potential on the grid (host or device) */
+  int nproj;             /* number of projectors (may be 0) */
+  const double *beta;    /* [nproj][npw_h] complex projector coefficients (host or device) */
+  const double *dij;     /* [nproj] projector strengths D_j (host) */
+  int nocc;              /* occupied orbitals (closed shell, 2 electrons each) */
+  const double *psi;     /* [nocc][npw_h] complex occupied orbitals, orthonormal and real in r,
+                            (host or device); NULL: the library computes them (wdf_ground_state) */
+  const double *eps;     /* [nocc] their eigenvalues (host); NULL when psi is NULL */
+  int mem;               /* wdf_mem of vloc_r, beta and psi */
+} wdf_system;
+
+typedef struct wdf_options {
+  int precision;     /* wdf_precision, default WDF_MIXED */
+  int precond;       /* wdf_precond, default WDF_PRECOND_TPA */
+  double cg_tol;     /* stop a solve at ||b - A x|| <= cg_tol ||b|| (default 1e-8) */
+  int cg_maxiter;    /* CG iterations per solve, summed over refinement steps (default 1000) */
+  double inner_tol;  /* WDF_MIXED: relative reduction asked of each FP32 inner solve (1e-5) */
+  double alpha;      /* shift of the occupied space in the Sternheimer operator; <= 0: auto
+                        (eps_max - eps_min + 1 hartree) */
+  int max_batch;     /* most Sternheimer solves resident at once (0: all of a block) */
+  double gs_tol;     /* ground state: residual norm per orbital (default 1e-10) */
+  int gs_maxiter;    /* ground state Davidson iterations (default 300) */
+  int gs_extra;      /* ground state: extra states beyond nocc carried in the Davidson (default 8) */
+  void *stream;      /* cudaStream_t for all work of the context (NULL: default stream) */
+  int device;        /* CUDA device ordinal (default 0) */
+} wdf_options;
+
+/* Statistics of the last apply / Davidson call. */
+typedef struct wdf_stats {
+  int64_t nsolve;          /* Sternheimer solves done */
+  int64_t cg_iters;        /* CG iterations summed over solves (inner FP32 + FP64) */
+  int32_t cg_iters_max;    /* most iterations of one solve */
+  int32_t refinements;     /* WDF_MIXED: FP64 residual evaluations per solve, maximum */
+  double max_residual;     /* largest final ||b - A x|| / ||b|| over solves (FP64) */
+  int64_t napply;          /* chi0bar applications (perturbation vectors) */
+  int32_t davidson_iters;  /* Davidson iterations */
+  int32_t converged;       /* 1 if every requested quantity met its tolerance */
+  double ms;               /* wall time of the call, milliseconds */
+} wdf_stats;
+
+/* Fill *opt with the defaults listed above. */
+void wdf_default_options(wdf_options *opt);
+
+/* Create a context: validate and copy the system to the GPU, build the plane-wave layout and
+ * FFT plans, and, if sys->psi is NULL, compute the nocc lowest eigenpairs of H (Eq. (1)) by the
+ * library's block Davidson with the TPA preconditioner to opt->gs_tol.
+ * out: receives the context (NULL on failure). opt: NULL for defaults.
+ * Errors: WDF_EINVAL (sizes, Miller set not a half sphere, grid too small for the sphere or not
+ * 2,3,5-smooth), WDF_ENOMEM, WDF_ECUDA, WDF_ESTATE (no usable GPU), WDF_ENOCONV (ground state
+ * did not converge: the context is still created and usable), WDF_ENAN. */
+int wdf_setup_hamiltonian(wdf_ctx **out, const wdf_system *sys, const wdf_options *opt);
+
+/* Release the context and all its device memory. NULL is ignored. */
+void wdf_destroy(wdf_ctx *ctx);
+
+/* Copy the occupied eigenpairs into eps[nocc] (host) and, if psi is not NULL, psi[nocc][npw_h]
+ * complex (host or device per mem). Orbitals are real in r and orthonormal. */
+int wdf_get_orbitals(wdf_ctx *ctx, double *eps, double *psi, int mem);
+
+/* Apply H (Eq. (1): kinetic + local + Kleinman-Bylander) to nvec half-sphere vectors.
+ * in, out: [nvec][npw_h] complex, host or device per mem; out may alias in. */
+int wdf_apply_hamiltonian(wdf_ctx *ctx, int nvec, const double *in, double *out, int mem);
+
+/* Solve the Sternheimer equations of Sec. 2.1 for nsolve right-hand sides:
+ * (H - eps_v + alpha P) x_k = rhs_k with v = vidx[k], P the projector on the occupied space,
+ * to ||rhs_k - A x_k|| <= cg_tol ||rhs_k||. For rhs_k orthogonal to the occupied space this is
+ * the unique solution of (H - eps_v) x = rhs in that complement.
+ * vidx: [nsolve] (host), each in [0, nocc). rhs, x: [nsolve][npw_h] complex (host or device).
+ * st: optional statistics. Errors: WDF_EINVAL, WDF_ENOCONV (x holds the last iterate). */
+int wdf_sternheimer(wdf_ctx *ctx, int nsolve, const int32_t *vidx, const double *rhs, double *x,
+                    int mem, wdf_stats *st);
+
+/* chi0bar phi for npert perturbations (Sec. 2.1: chi0bar = v^1/2 chi0 v^1/2 with the density
+ * response by DFPT). For each perturbation p and occupied orbital v: dV_p = v^1/2 phi_p in real
+ * space, one Sternheimer solve (H - eps_v) dpsi_vp = -Q dV_p psi_v to cg_tol, then
+ * drho_p = 4 sum_v psi_v dpsi_vp and out_p = v^1/2 drho_p, v^1/2(G) = sqrt(4 pi)/|G|, zero at
+ * G = 0.
+ * phi: [npert][npw_h] complex, orthonormal or not; the G = 0 entry is ignored.
+ * out: [npert][npw_h] complex = chi0bar phi; may alias phi. drho: optional [npert][npw_h]
+ * complex plane-wave coefficients <b_G|drho_p>. All host or device per mem.
+ * Errors: WDF_EINVAL, WDF_ENOMEM, WDF_ECUDA, WDF_ENOCONV (outputs from the last iterates). */
+int wdf_apply_chi0(wdf_ctx *ctx, int npert, const double *phi, double *out, double *drho, int mem,
+                   wdf_stats *st);
+
+/* PDEP: the neig algebraically lowest eigenpairs of chi0bar (Eq. (5): lambda_a, phibar_a) by
+ * block Davidson. Start block: the nguess vectors of guess (G = 0 entries ignored), at least
+ * neig of them; expansion by the residuals of the unconverged Ritz pairs, two-pass classical
+ * Gram-Schmidt in FP64 (vectors below 1e-12 after projection dropped), restart from the neig
+ * Ritz vectors when the basis would exceed nbasis_max (0: 4*neig); converged when
+ * ||chi0bar x_a - lambda_a x_a|| <= tol for all a.
+ * lambda: [neig] ascending (host). phibar: [neig][npw_h] complex orthonormal (host or device).
+ * Errors: WDF_EINVAL, WDF_ENOCONV (best Ritz pairs returned), others as wdf_apply_chi0. */
+int wdf_pdep_davidson(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, double tol,
+                      int nguess, const double *guess, double *lambda, double *phibar, int mem,
+                      wdf_stats *st);
+
+/* Static text for a status code. */
+const char *wdf_strerror(int status);
+
+/* Message of the last failure in ctx (or of the last failed setup when ctx is NULL). */
+const char *wdf_last_error(const wdf_ctx *ctx);
+
+/* Library version string. */
+const char *wdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WDF_H */

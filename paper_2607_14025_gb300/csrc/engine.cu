@@ -1,0 +1,639 @@
+// Solver engine: Hamiltonian and Sternheimer operators, preconditioned CG with iterative
+// refinement, chi0bar application by DFPT and the block Davidson shared by the ground state and
+// PDEP (paper Sec. 2.1 for the method, Sec. 3.3 for the single Davidson implementation).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "engine.cuh"
+
+namespace wdf {
+
+// ---------------------------------------------------------------------------------------------
+// small local kernels
+
+template <typename T>
+__global__ void k_split_pairs(const cplx<T> *__restrict__ grid, int npair, size_t ngrid, T *__restrict__ out, int nreal) {
+  const size_t tot = (size_t)npair * ngrid;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / ngrid);
+    const size_t i = t % ngrid;
+    const cplx<T> v = grid[t];
+    out[(size_t)(2 * q) * ngrid + i] = v.x;
+    if (2 * q + 1 < nreal) out[(size_t)(2 * q + 1) * ngrid + i] = v.y;
+  }
+}
+
+__global__ void k_scale_elems(Geo g, cplx<double> *__restrict__ y, const cplx<double> *__restrict__ x, const double *__restrict__ tab,
+                              int n) {
+  const size_t tot = (size_t)n * g.ld;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = cscal<double>(x[t], tab[t % g.ld]);
+}
+
+__global__ void k_gather_shift(const int *__restrict__ vidx, const double *__restrict__ eps, double *__restrict__ shift, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) shift[t] = eps[vidx[t]];
+}
+
+__global__ void k_sum_chunks(const double *__restrict__ part, int n, int nchunk, double *__restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(size_t)t * nchunk + c];
+  out[t] = s;
+}
+
+static int grid_for(size_t tot) { return (int)std::min<size_t>(8192, (tot + 255) / 256); }
+
+// ---------------------------------------------------------------------------------------------
+// precision traits
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static const FftCtx<double> &f(wdf_ctx *c) { return c->f64; }
+  static const double *vloc(wdf_ctx *c) { return c->vloc64.as<double>(); }
+  static const cplx<double> *U(wdf_ctx *c) { return c->U64.as<cplx<double>>(); }
+  static const double *kp(wdf_ctx *c) { return c->kp64.as<double>(); }
+  static wdf_ctx::Cg &cg(wdf_ctx *c) { return c->cg64; }
+};
+template <> struct Prec<float> {
+  static const FftCtx<float> &f(wdf_ctx *c) { return c->f32; }
+  static const float *vloc(wdf_ctx *c) { return c->vloc32.as<float>(); }
+  static const cplx<float> *U(wdf_ctx *c) { return c->U32.as<cplx<float>>(); }
+  static const float *kp(wdf_ctx *c) { return c->kp32.as<float>(); }
+  static wdf_ctx::Cg &cg(wdf_ctx *c) { return c->cg32; }
+};
+
+static const double *zeros(wdf_ctx *c, size_t n) {
+  if (c->zeros.cap < n * sizeof(double)) {
+    c->zeros.ensure(n * sizeof(double));
+    WDF_CUDA_TRY(cudaMemsetAsync(c->zeros.p, 0, c->zeros.cap, c->st));
+  }
+  return c->zeros.as<double>();
+}
+
+static double *gram_work(wdf_ctx *c, int na, int nb, int ldo, size_t &cap) {
+  const size_t need = gram_work_doubles(c->geo, na, nb, ldo);
+  c->gramw.ensure(std::max<size_t>(need, 1) * sizeof(double));
+  cap = c->gramw.cap / sizeof(double);
+  return c->gramw.as<double>();
+}
+
+template <typename T>
+static void gram(wdf_ctx *c, const cplx<T> *A, int na, const cplx<T> *B, int nb, double *out, int ldo) {
+  size_t cap;
+  double *w = gram_work(c, na, nb, ldo, cap);
+  launch_gram<T>(c->geo, A, na, B, nb, out, ldo, w, cap, c->st);
+}
+
+// per-vector inner products <A_s, B_s> into a device array (n doubles)
+template <typename T>
+static void dots(wdf_ctx *c, const cplx<T> *A, const cplx<T> *B, int n, double *out) {
+  const int nch = dot_chunks(c->geo);
+  wdf_ctx::Cg &w = Prec<T>::cg(c);
+  w.part1.ensure(sizeof(double) * (size_t)n * nch);
+  launch_dot_partial<T>(c->geo, A, B, n, w.part1.as<double>(), nch, c->st);
+  k_sum_chunks<<<(n + 127) / 128, 128, 0, c->st>>>(w.part1.as<double>(), n, nch, out);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+static std::vector<double> to_host(wdf_ctx *c, const double *d, size_t n) {
+  std::vector<double> h(n);
+  if (n) {
+    WDF_CUDA_TRY(cudaMemcpyAsync(h.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+  }
+  return h;
+}
+
+// ---------------------------------------------------------------------------------------------
+// operators
+
+// Y = (H - shift_s) X (+ alpha P X when with_alpha); H = 1/2|G|^2 + V_loc + sum_j beta_j D_j beta_j^T
+template <typename T>
+void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const double *shift, bool with_alpha) {
+  if (n <= 0) return;
+  const FftCtx<T> &f = Prec<T>::f(c);
+  const Geo &g = c->geo;
+  wdf_ctx::Cg &w = Prec<T>::cg(c);
+  const int npair = (n + 1) / 2;
+  w.cb.ensure(sizeof(cplx<T>) * (size_t)npair * g.n3 * g.ldcb);
+  cplx<T> *cb = w.cb.as<cplx<T>>();
+  launch_zpass_g2r<T>(f, X, n, cb, c->st);
+  PlaneArgs<T> pa;
+  pa.cb = cb;
+  pa.field = Prec<T>::vloc(c);
+  launch_plane<T>(f, OP_VLOC, npair, pa, c->st);
+  EpiArgs<T> ea;
+  ea.Y = Y;
+  ea.X = X;
+  ea.shift = shift ? shift : zeros(c, n);
+  ea.scale = (T)(1.0 / (double)c->ngrid);
+  launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, n, ea, c->st);
+  const int M = c->nproj + (with_alpha ? c->nocc : 0);
+  if (M > 0) {
+    w.S.ensure(sizeof(double) * (size_t)M * n);
+    gram<T>(c, Prec<T>::U(c), M, X, n, w.S.as<double>(), n);
+    launch_lincomb<T>(g, Y, n, Prec<T>::U(c), M, w.S.as<double>(), n, c->lrd.as<double>(), 1.0, c->st);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// preconditioned conjugate gradients on (H - eps_v + alpha P) d = b, one solve per row
+
+template <typename T>
+static void cg_solve(wdf_ctx *c, const cplx<T> *b, cplx<T> *x, int n, int maxiter, std::vector<int> &iters) {
+  const Geo &g = c->geo;
+  wdf_ctx::Cg &w = Prec<T>::cg(c);
+  const size_t vb = sizeof(cplx<T>) * (size_t)n * g.ld;
+  w.r.ensure(vb);
+  w.z.ensure(vb);
+  w.p.ensure(vb);
+  w.Ap.ensure(vb);
+  const int nch = dot_chunks(g);
+  w.part1.ensure(sizeof(double) * (size_t)n * nch);
+  w.part2.ensure(sizeof(double) * (size_t)n * nch);
+  w.dbl.ensure(sizeof(double) * 4 * (size_t)n);
+  w.ints.ensure(sizeof(int) * (2 * (size_t)n + 1));
+  CgState s;
+  double *d = w.dbl.as<double>();
+  s.rz = d;
+  s.rz_new = d + n;
+  s.pap = d + 2 * n;
+  s.rr = d + 3 * n;
+  s.thr = c->thr.as<double>();
+  s.shift = c->shift.as<double>();
+  s.part1 = w.part1.as<double>();
+  s.part2 = w.part2.as<double>();
+  int *ii = w.ints.as<int>();
+  s.active = ii;
+  s.iters = ii + n;
+  s.nactive = ii + 2 * n;
+  s.vidx = c->vidx_dev.as<int>();
+  cplx<T> *r = w.r.as<cplx<T>>(), *z = w.z.as<cplx<T>>(), *p = w.p.as<cplx<T>>(), *Ap = w.Ap.as<cplx<T>>();
+  cudaStream_t st = c->st;
+  const T *K = c->opt.precond == WDF_PRECOND_TPA ? Prec<T>::kp(c) : nullptr;
+
+  WDF_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
+  WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
+  WDF_CUDA_TRY(cudaMemsetAsync(ii, 0, sizeof(int) * (2 * (size_t)n + 1), st));
+  launch_cg_start<T>(g, r, z, p, K, s, n, nch, st);
+  launch_cg_scalars(s, n, nch, 2, maxiter, st);
+  int nact = 0;
+  WDF_CUDA_TRY(cudaMemcpyAsync(&nact, s.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WDF_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int it = 0; it < maxiter && nact > 0; ++it) {
+    apply_operator<T>(c, p, Ap, n, s.shift, true);
+    launch_dot_partial<T>(g, p, Ap, n, s.part1, nch, st);
+    launch_cg_scalars(s, n, nch, 0, maxiter, st);
+    launch_cg_update<T>(g, x, r, z, p, Ap, K, s, n, nch, st);
+    WDF_CUDA_TRY(cudaMemsetAsync(s.nactive, 0, sizeof(int), st));
+    launch_cg_scalars(s, n, nch, 1, maxiter, st);
+    launch_cg_direction<T>(g, p, z, s, n, st);
+    WDF_CUDA_TRY(cudaMemcpyAsync(&nact, s.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WDF_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  iters.resize(n);
+  WDF_CUDA_TRY(cudaMemcpyAsync(iters.data(), s.iters, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  WDF_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// FP64 outer loop: r = b - A x in FP64, inner solve A d = r (FP64 or FP32), x += d.
+void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const int *vidx_host, int n, SolveStats &ss) {
+  if (n <= 0) return;
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  const bool mixed = c->opt.precision == WDF_MIXED;
+  const size_t vb = sizeof(cplx<double>) * (size_t)n * g.ld;
+  c->vidx_dev.ensure(sizeof(int) * n);
+  c->shift.ensure(sizeof(double) * n);
+  c->thr.ensure(sizeof(double) * n);
+  WDF_CUDA_TRY(cudaMemcpyAsync(c->vidx_dev.p, vidx_host, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  k_gather_shift<<<(n + 127) / 128, 128, 0, st>>>(c->vidx_dev.as<int>(), c->eps_dev.as<double>(), c->shift.as<double>(), n);
+  WDF_CUDA_TRY(cudaGetLastError());
+  c->rr.ensure(vb);
+  c->rAx.ensure(vb);
+  cplx<double> *r = c->rr.as<cplx<double>>(), *Ax = c->rAx.as<cplx<double>>();
+  double *nrm = c->dv_small.as<double>();
+  c->dv_small.ensure(sizeof(double) * 2 * (size_t)n);
+  nrm = c->dv_small.as<double>();
+  dots<double>(c, b, b, n, nrm);
+  const std::vector<double> bb = to_host(c, nrm, n);
+  WDF_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
+  WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
+  const double tol = c->opt.cg_tol;
+  const int maxref = mixed ? 12 : 6;
+  std::vector<int> iters_total(n, 0), it;
+  std::vector<double> rr(n, 0.0);
+  std::vector<double> thr(n);
+  bool conv = false;
+  ss.refinements = 0;
+  const bool trace = std::getenv("WDF_TRACE") != nullptr;
+  for (int ref = 0; ref <= maxref; ++ref) {
+    dots<double>(c, r, r, n, nrm);
+    rr = to_host(c, nrm, n);
+    int nact = 0, nunconv = 0;
+    double worst = 0.0;
+    for (int s = 0; s < n; ++s) {
+      const bool unconv = bb[s] > 0.0 && rr[s] > tol * tol * bb[s];
+      const bool act = unconv && iters_total[s] < c->opt.cg_maxiter;
+      if (!std::isfinite(rr[s])) throw ApiFailure(WDF_ENAN, "non-finite residual in a Sternheimer solve");
+      if (unconv) ++nunconv;
+      if (bb[s] > 0.0) worst = std::max(worst, std::sqrt(rr[s] / bb[s]));
+      if (act) {
+        ++nact;
+        double eta = 0.5 * tol * std::sqrt(bb[s] / rr[s]);
+        if (mixed) eta = std::max(eta, c->opt.inner_tol);
+        eta = std::max(eta, 1e-15);
+        thr[s] = eta * eta * rr[s];
+      } else {
+        thr[s] = 1e300;  // start inactive
+      }
+    }
+    if (trace) {
+      int itmax = 0;
+      for (int s = 0; s < n; ++s) itmax = std::max(itmax, iters_total[s]);
+      fprintf(stderr, "[wdf] refinement %d: %d of %d solves above tol, worst rel residual %.3e, max iterations %d\n", ref,
+              nunconv, n, worst, itmax);
+    }
+    if (nunconv == 0) {
+      conv = true;
+      break;
+    }
+    if (nact == 0) break;  // iteration budget spent
+    if (ref == maxref) break;
+    ss.refinements = ref + 1;
+    WDF_CUDA_TRY(cudaMemcpyAsync(c->thr.p, thr.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    int budget = 0;
+    for (int s = 0; s < n; ++s) budget = std::max(budget, c->opt.cg_maxiter - iters_total[s]);
+    if (mixed) {
+      auto &w = c->cg32;
+      w.x.ensure(sizeof(cplx<float>) * (size_t)n * g.ld);
+      c->rwork.ensure(sizeof(cplx<float>) * (size_t)n * g.ld);
+      cplx<float> *r32 = c->rwork.as<cplx<float>>(), *d32 = w.x.as<cplx<float>>();
+      launch_convert<double, float>(g, (float *)r32, (const double *)r, 2 * (size_t)n * g.ld, st);
+      cg_solve<float>(c, r32, d32, n, budget, it);
+      // x += d ; reuse Ax as FP64 staging of d
+      launch_convert<float, double>(g, (double *)Ax, (const float *)d32, 2 * (size_t)n * g.ld, st);
+      launch_axpby<double>(g, x, Ax, n, 1.0, 1.0, st);
+    } else {
+      auto &w = c->cg64;
+      w.x.ensure(vb);
+      cplx<double> *d = w.x.as<cplx<double>>();
+      cg_solve<double>(c, r, d, n, budget, it);
+      launch_axpby<double>(g, x, d, n, 1.0, 1.0, st);
+    }
+    for (int s = 0; s < n; ++s) iters_total[s] += it[s];
+    // r = b - A x in FP64
+    apply_operator<double>(c, x, Ax, n, c->shift.as<double>(), true);
+    WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
+    launch_axpby<double>(g, r, Ax, n, -1.0, 1.0, st);
+  }
+  ss.converged = conv;
+  ss.iters = 0;
+  ss.iters_max = 0;
+  ss.max_res = 0.0;
+  for (int s = 0; s < n; ++s) {
+    ss.iters += iters_total[s];
+    ss.iters_max = std::max(ss.iters_max, iters_total[s]);
+    if (bb[s] > 0) ss.max_res = std::max(ss.max_res, std::sqrt(rr[s] / bb[s]));
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// chi0bar by DFPT (paper Sec. 2.1). phi: npert internal FP64 vectors (G = 0 ignored).
+
+void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<double> *out, cplx<double> *drho,
+                         SolveStats &ss) {
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  const FftCtx<double> &f = c->f64;
+  const int npp = (npert + 1) / 2, np2 = 2 * npp, nocc = c->nocc;
+  const size_t ngrid = c->ngrid;
+  const size_t cbpair = (size_t)g.n3 * g.ldcb;
+  // x = v^1/2 phi (extra zero row when npert is odd)
+  c->xpert.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+  cplx<double> *xp = c->xpert.as<cplx<double>>();
+  WDF_CUDA_TRY(cudaMemsetAsync(xp, 0, sizeof(cplx<double>) * (size_t)np2 * g.ld, st));
+  k_scale_elems<<<grid_for((size_t)npert * g.ld), 256, 0, st>>>(g, xp, phi, c->t_vhalf.as<double>(), npert);
+  WDF_CUDA_TRY(cudaGetLastError());
+  // dV pairs in real space: dV_2pp + i dV_2pp+1 = ifft(x_2pp + i x_2pp+1)
+  c->dvgrid.ensure(sizeof(cplx<double>) * (size_t)npp * ngrid);
+  cplx<double> *dv = c->dvgrid.as<cplx<double>>();
+  {
+    auto &w = c->cg64;
+    w.cb.ensure(sizeof(cplx<double>) * (size_t)npp * cbpair);
+    launch_zpass_g2r<double>(f, xp, np2, w.cb.as<cplx<double>>(), st);
+    PlaneArgs<double> pa;
+    pa.cb = w.cb.as<cplx<double>>();
+    pa.grid = dv;
+    launch_plane<double>(f, OP_G2R, npp, pa, st);
+  }
+  // perturbation pairs per chunk so that at most max_batch solves are resident
+  int cpp = npp;
+  if (c->opt.max_batch > 0) cpp = std::max(1, std::min(npp, c->opt.max_batch / (2 * nocc)));
+  // results go to scratch with an even number of rows (the last pair may hold a phantom row)
+  c->chi_out.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+  c->chi_drho.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+  cplx<double> *dr = c->chi_drho.as<cplx<double>>(), *ou = c->chi_out.as<cplx<double>>();
+  ss = SolveStats();
+  SolveStats sc;
+  for (int pp0 = 0; pp0 < npp; pp0 += cpp) {
+    const int pp1 = std::min(npp, pp0 + cpp);
+    const int nq = (pp1 - pp0) * nocc, ns = 2 * nq;
+    // right-hand sides b_vp = -Q fft_n(dV_p psi_v)
+    c->rb.ensure(sizeof(cplx<double>) * (size_t)ns * g.ld);
+    c->rx.ensure(sizeof(cplx<double>) * (size_t)ns * g.ld);
+    cplx<double> *b = c->rb.as<cplx<double>>(), *x = c->rx.as<cplx<double>>();
+    auto &w = c->cg64;
+    w.cb.ensure(sizeof(cplx<double>) * (size_t)nq * cbpair);
+    cplx<double> *cb = w.cb.as<cplx<double>>();
+    {
+      PlaneArgs<double> pa;
+      pa.cb = cb;
+      pa.field = c->psir64.as<double>();
+      pa.grid = dv + (size_t)pp0 * ngrid;
+      pa.nocc = nocc;
+      launch_plane<double>(f, OP_PROD_R2G, nq, pa, st);
+      EpiArgs<double> ea;
+      ea.Y = b;
+      ea.scale = 1.0 / (double)ngrid;
+      launch_zpass_r2g<double>(f, EPI_STORE, cb, ns, ea, st);
+      const cplx<double> *psi = c->U64.as<cplx<double>>() + (size_t)c->nproj * g.ld;
+      w.S.ensure(sizeof(double) * (size_t)nocc * ns);
+      gram<double>(c, psi, nocc, b, ns, w.S.as<double>(), ns);
+      launch_lincomb<double>(g, b, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
+    }
+    std::vector<int> vidx(ns);
+    for (int s = 0; s < ns; ++s) vidx[s] = (s / 2) % nocc;
+    sternheimer_solve(c, b, x, vidx.data(), ns, sc);
+    ss.iters += sc.iters;
+    ss.iters_max = std::max(ss.iters_max, sc.iters_max);
+    ss.refinements = std::max(ss.refinements, sc.refinements);
+    ss.max_res = std::max(ss.max_res, sc.max_res);
+    ss.converged = ss.converged && sc.converged;
+    // drho_p = (4/Omega) fft_n(sum_v psi_v ifft(dpsi_vp)); out = v^1/2 drho
+    w.cb.ensure(sizeof(cplx<double>) * (size_t)nq * cbpair);
+    cb = w.cb.as<cplx<double>>();
+    c->cb2.ensure(sizeof(cplx<double>) * (size_t)(pp1 - pp0) * cbpair);
+    c->accgrid.ensure(sizeof(cplx<double>) * (size_t)(pp1 - pp0) * ngrid);
+    launch_zpass_g2r<double>(f, x, ns, cb, st);
+    PlaneArgs<double> pa;
+    pa.cb = cb;
+    pa.cb2 = c->cb2.as<cplx<double>>();
+    pa.field = c->psir64.as<double>();
+    pa.grid = c->accgrid.as<cplx<double>>();
+    pa.nocc = nocc;
+    launch_plane<double>(f, OP_ACCUM, pp1 - pp0, pa, st);
+    EpiArgs<double> ea;
+    ea.Y = dr + (size_t)(2 * pp0) * g.ld;
+    ea.Y2 = ou + (size_t)(2 * pp0) * g.ld;
+    ea.vhalf = c->t_vhalf.as<double>();
+    ea.scale = 4.0 / (c->omega * (double)ngrid);
+    launch_zpass_r2g<double>(f, EPI_DRHO, c->cb2.as<cplx<double>>(), 2 * (pp1 - pp0), ea, st);
+  }
+  const size_t nb = sizeof(cplx<double>) * (size_t)npert * g.ld;
+  WDF_CUDA_TRY(cudaMemcpyAsync(out, ou, nb, cudaMemcpyDeviceToDevice, st));
+  if (drho) WDF_CUDA_TRY(cudaMemcpyAsync(drho, dr, nb, cudaMemcpyDeviceToDevice, st));
+}
+
+// ---------------------------------------------------------------------------------------------
+// block Davidson
+
+static void copy_rows(wdf_ctx *c, cplx<double> *dst, const cplx<double> *src, int n) {
+  if (n <= 0 || dst == src) return;
+  WDF_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(cplx<double>) * (size_t)n * c->geo.ld, cudaMemcpyDeviceToDevice, c->st));
+}
+
+// Make rows [nb, nb + nnew) of V orthonormal to rows [0, nb) and to each other: unit scaling,
+// two passes of block classical Gram-Schmidt against the old rows, then vector by vector (two
+// passes) within the block; vectors left with norm < drop are removed. Returns the number kept
+// (compacted to rows nb ...).
+static int orthonormalise(wdf_ctx *c, cplx<double> *V, int nb, int nnew, double drop) {
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  if (nnew <= 0) return 0;
+  cplx<double> *Nw = V + (size_t)nb * g.ld;
+  double *sm = c->dv_small.as<double>();
+  double *neg = c->dv_neg.as<double>();
+  // unit scaling
+  dots<double>(c, Nw, Nw, nnew, sm);
+  std::vector<double> n2 = to_host(c, sm, nnew);
+  std::vector<double> inv(nnew);
+  for (int i = 0; i < nnew; ++i) inv[i] = n2[i] > 0 ? 1.0 / std::sqrt(n2[i]) : 0.0;
+  WDF_CUDA_TRY(cudaMemcpyAsync(sm, inv.data(), sizeof(double) * nnew, cudaMemcpyHostToDevice, st));
+  launch_scale_rows<double>(g, Nw, sm, nnew, st);
+  double *C = c->dv_Y.as<double>();  // scratch nb x nnew
+  for (int pass = 0; pass < 2 && nb > 0; ++pass) {
+    gram<double>(c, V, nb, Nw, nnew, C, nnew);
+    launch_lincomb<double>(g, Nw, nnew, V, nb, C, nnew, neg, 1.0, st);
+  }
+  int kept = 0;
+  for (int i = 0; i < nnew; ++i) {
+    cplx<double> *vi = Nw + (size_t)i * g.ld;
+    cplx<double> *base = Nw;  // kept rows are Nw[0 .. kept)
+    for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+      gram<double>(c, base, kept, vi, 1, C, 1);
+      launch_lincomb<double>(g, vi, 1, base, kept, C, 1, neg, 1.0, st);
+    }
+    dots<double>(c, vi, vi, 1, sm);
+    const double nn = std::sqrt(to_host(c, sm, 1)[0]);
+    if (!(nn >= drop)) continue;
+    const double s = 1.0 / nn;
+    WDF_CUDA_TRY(cudaMemcpyAsync(sm, &s, sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_scale_rows<double>(g, vi, sm, 1, st);
+    copy_rows(c, Nw + (size_t)kept * g.ld, vi, 1);
+    ++kept;
+  }
+  return kept;
+}
+
+DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nwant, int nkeep, int nbmax, int maxiter,
+                   double tol, bool zero_g0) {
+  (void)zero_g0;
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  DavResult res;
+  // after a restart the basis holds nkeep Ritz vectors plus at most nkeep new ones
+  nbmax = std::max(nbmax, 2 * nkeep);
+  const size_t vb = sizeof(cplx<double>) * (size_t)g.ld;
+  c->dv_V.ensure(vb * (size_t)std::max(nbmax, n0));
+  c->dv_W.ensure(vb * (size_t)std::max(nbmax, n0));
+  c->dv_X.ensure(vb * (size_t)nkeep);
+  c->dv_AX.ensure(vb * (size_t)nkeep);
+  c->dv_R.ensure(vb * (size_t)nkeep);
+  c->dv_H.ensure(sizeof(double) * (size_t)nbmax * nbmax);
+  c->dv_Y.ensure(sizeof(double) * (size_t)std::max(nbmax, n0) * std::max(nbmax, n0));
+  c->dv_theta.ensure(sizeof(double) * nbmax);
+  c->dv_jac.ensure(sizeof(double) * jacobi_work_doubles(nbmax));
+  c->dv_jint.ensure(sizeof(int) * 4);
+  c->dv_small.ensure(sizeof(double) * (size_t)std::max(nbmax, n0) * 2);
+  c->dv_neg.ensure(sizeof(double) * (size_t)std::max(nbmax, n0));
+  {
+    std::vector<double> neg(std::max(nbmax, n0), -1.0);
+    WDF_CUDA_TRY(cudaMemcpyAsync(c->dv_neg.p, neg.data(), sizeof(double) * neg.size(), cudaMemcpyHostToDevice, st));
+  }
+  cplx<double> *V = c->dv_V.as<cplx<double>>(), *W = c->dv_W.as<cplx<double>>();
+  cplx<double> *X = c->dv_X.as<cplx<double>>(), *AX = c->dv_AX.as<cplx<double>>(), *R = c->dv_R.as<cplx<double>>();
+  double *H = c->dv_H.as<double>(), *Y = c->dv_Y.as<double>(), *theta = c->dv_theta.as<double>();
+  const double drop = 1e-12;
+  copy_rows(c, V, V0, n0);
+  int nb = orthonormalise(c, V, 0, n0, drop);
+  if (nb < nkeep) throw ApiFailure(WDF_EINVAL, "start block has fewer independent vectors than requested eigenpairs");
+  if (nb > nbmax) nb = nbmax;
+  op.apply(V, W, nb);
+  res.napply = nb;
+  std::vector<double> th, rn;
+  for (int it = 1; it <= maxiter; ++it) {
+    res.iters = it;
+    gram<double>(c, V, nb, W, nb, H, nb);
+    jacobi_eigh(H, Y, theta, nb, c->dv_jac.as<double>(), c->dv_jint.as<int>(), st);
+    const int k = std::min(nkeep, nb);
+    launch_lincomb<double>(g, X, k, V, nb, Y, nb, nullptr, 0.0, st);
+    launch_lincomb<double>(g, AX, k, W, nb, Y, nb, nullptr, 0.0, st);
+    launch_ritz_residual(g, R, AX, X, theta, k, st);
+    dots<double>(c, R, R, k, c->dv_small.as<double>());
+    rn = to_host(c, c->dv_small.as<double>(), k);
+    th = to_host(c, theta, k);
+    bool all = true;
+    std::vector<int> unconv;
+    for (int a = 0; a < k; ++a) {
+      rn[a] = std::sqrt(std::max(0.0, rn[a]));
+      const bool ok = rn[a] <= tol;
+      if (!ok) unconv.push_back(a);
+      if (a < nwant && !ok) all = false;
+    }
+    res.lam = th;
+    res.resnorm = rn;
+    if (all) {
+      res.converged = true;
+      break;
+    }
+    if (it == maxiter) break;
+    const int nu = (int)unconv.size();
+    if (nb + nu > nbmax) {  // restart from the Ritz vectors
+      copy_rows(c, V, X, k);
+      copy_rows(c, W, AX, k);
+      nb = k;
+    }
+    cplx<double> *Nw = V + (size_t)nb * g.ld;
+    for (int i = 0; i < nu; ++i) copy_rows(c, Nw + (size_t)i * g.ld, R + (size_t)unconv[i] * g.ld, 1);
+    if (op.precondition()) {
+      // TPA with the kinetic energy of each Ritz vector
+      double *tk = c->dv_small.as<double>();
+      c->rwork.ensure(sizeof(double) * (size_t)nu * g.ld);
+      for (int i = 0; i < nu; ++i) launch_kinetic(g, X + (size_t)unconv[i] * g.ld, 1, tk + i, st);
+      launch_tpa_table<double>(g, c->rwork.as<double>(), tk, nu, st);
+      launch_mul_table<double>(g, Nw, c->rwork.as<double>(), nu, st);
+    }
+    const int kept = orthonormalise(c, V, nb, nu, drop);
+    if (kept == 0) break;
+    op.apply(Nw, W + (size_t)nb * g.ld, kept);
+    res.napply += kept;
+    nb += kept;
+  }
+  return res;
+}
+
+// ---------------------------------------------------------------------------------------------
+// ground state of H (paper Eq. (1)) by the same Davidson, TPA-preconditioned
+
+struct HamOp : DavOp {
+  wdf_ctx *c;
+  explicit HamOp(wdf_ctx *cc) : c(cc) {}
+  void apply(const cplx<double> *X, cplx<double> *Y, int n) override { apply_operator<double>(c, X, Y, n, nullptr, false); }
+  bool precondition() const override { return true; }
+};
+
+void ground_state(wdf_ctx *c) {
+  const Geo &g = c->geo;
+  const Layout &L = c->lay;
+  const int nev = std::min(c->nocc + std::max(0, c->opt.gs_extra), 2 * L.nint - L.len0);
+  // start block: the plane waves of lowest kinetic energy as cos / sin pairs (no random numbers)
+  std::vector<int> order;
+  for (int e = 0; e < L.nint; ++e) {
+    if (L.e_col[e] == 0 && L.e_z[e] < 0) continue;  // column (0,0): one of each +-z pair
+    order.push_back(e);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return L.g2[a] < L.g2[b]; });
+  const int n0 = nev;
+  std::vector<cplx<double>> h0((size_t)n0 * g.ld, mkc<double>(0, 0));
+  int made = 0;
+  for (size_t t = 0; t < order.size() && made < n0; ++t) {
+    const int e = order[t];
+    const bool self = (L.e_col[e] == 0 && L.e_z[e] == 0);
+    for (int kind = 0; kind < (self ? 1 : 2) && made < n0; ++kind) {
+      cplx<double> *v = h0.data() + (size_t)made * g.ld;
+      v[e] = kind == 0 ? mkc<double>(1, 0) : mkc<double>(0, 1);
+      if (L.e_col[e] == 0 && L.e_z[e] > 0) {  // mirror inside column (0,0)
+        const int e2 = L.col_off[0] + (-L.e_z[e] - L.col_zlo[0]);
+        v[e2] = kind == 0 ? mkc<double>(1, 0) : mkc<double>(0, -1);
+      }
+      ++made;
+    }
+  }
+  c->rx.ensure(sizeof(cplx<double>) * h0.size());
+  WDF_CUDA_TRY(cudaMemcpyAsync(c->rx.p, h0.data(), sizeof(cplx<double>) * h0.size(), cudaMemcpyHostToDevice, c->st));
+  WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+  HamOp op(c);
+  DavResult r = davidson(c, op, c->rx.as<cplx<double>>(), n0, c->nocc, nev, 3 * nev, c->opt.gs_maxiter, c->opt.gs_tol, false);
+  c->eps.assign(r.lam.begin(), r.lam.begin() + c->nocc);
+  c->gap = (nev > c->nocc) ? r.lam[c->nocc] - r.lam[c->nocc - 1] : 0.0;
+  copy_rows(c, c->U64.as<cplx<double>>() + (size_t)c->nproj * g.ld, c->dv_X.as<cplx<double>>(), c->nocc);
+  WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (!r.converged) throw ApiFailure(WDF_ENOCONV, "ground state Davidson did not converge");
+}
+
+// tables that depend on the occupied orbitals
+void finish_setup(wdf_ctx *c) {
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  const int nocc = c->nocc, M = c->nproj + nocc;
+  double emin = c->eps[0], emax = c->eps[0];
+  for (double e : c->eps) {
+    emin = std::min(emin, e);
+    emax = std::max(emax, e);
+  }
+  c->alpha = c->opt.alpha > 0 ? c->opt.alpha : (emax - emin + 1.0);
+  std::vector<double> lrd(M);
+  for (int j = 0; j < c->nproj; ++j) lrd[j] = c->dij[j];
+  for (int v = 0; v < nocc; ++v) lrd[c->nproj + v] = c->alpha;
+  c->lrd.ensure(sizeof(double) * M);
+  WDF_CUDA_TRY(cudaMemcpyAsync(c->lrd.p, lrd.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+  c->eps_dev.ensure(sizeof(double) * nocc);
+  WDF_CUDA_TRY(cudaMemcpyAsync(c->eps_dev.p, c->eps.data(), sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
+  const cplx<double> *psi = c->U64.as<cplx<double>>() + (size_t)c->nproj * g.ld;
+  // psi_v(r) = ifft_u(c_v), two orbitals per complex transform
+  const int npair = (nocc + 1) / 2;
+  c->psir64.ensure(sizeof(double) * (size_t)nocc * c->ngrid);
+  c->psir32.ensure(sizeof(float) * (size_t)nocc * c->ngrid);
+  c->accgrid.ensure(sizeof(cplx<double>) * (size_t)npair * c->ngrid);
+  c->cg64.cb.ensure(sizeof(cplx<double>) * (size_t)npair * g.n3 * g.ldcb);
+  launch_zpass_g2r<double>(c->f64, psi, nocc, c->cg64.cb.as<cplx<double>>(), st);
+  PlaneArgs<double> pa;
+  pa.cb = c->cg64.cb.as<cplx<double>>();
+  pa.grid = c->accgrid.as<cplx<double>>();
+  launch_plane<double>(c->f64, OP_G2R, npair, pa, st);
+  k_split_pairs<double><<<grid_for((size_t)npair * c->ngrid), 256, 0, st>>>(c->accgrid.as<cplx<double>>(), npair, c->ngrid,
+                                                                           c->psir64.as<double>(), nocc);
+  WDF_CUDA_TRY(cudaGetLastError());
+  launch_convert<double, float>(g, c->psir32.as<float>(), c->psir64.as<double>(), (size_t)nocc * c->ngrid, st);
+  // TPA tables
+  c->tkin.ensure(sizeof(double) * nocc);
+  launch_kinetic(g, psi, nocc, c->tkin.as<double>(), st);
+  c->kp64.ensure(sizeof(double) * (size_t)nocc * g.ld);
+  c->kp32.ensure(sizeof(float) * (size_t)nocc * g.ld);
+  launch_tpa_table<double>(g, c->kp64.as<double>(), c->tkin.as<double>(), nocc, st);
+  launch_tpa_table<float>(g, c->kp32.as<float>(), c->tkin.as<double>(), nocc, st);
+  // FP32 copy of the projectors and orbitals
+  c->U32.ensure(sizeof(cplx<float>) * (size_t)M * g.ld);
+  launch_convert<double, float>(g, (float *)c->U32.p, (const double *)c->U64.p, 2 * (size_t)M * g.ld, st);
+  WDF_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+template void apply_operator<double>(wdf_ctx *, const cplx<double> *, cplx<double> *, int, const double *, bool);
+template void apply_operator<float>(wdf_ctx *, const cplx<float> *, cplx<float> *, int, const double *, bool);
+
+}  // namespace wdf

@@ -1,0 +1,127 @@
+// Host-side engine of libwdf.so: the context, its device buffers and the solver entry points.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace wdf {
+
+// Grow-only device buffer. ensure() may reallocate (contents are not kept).
+struct DBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  template <class T> T *as() const { return static_cast<T *>(p); }
+  void ensure(size_t bytes);
+  void release();
+};
+
+// Host copy of the plane-wave layout (see layout.cu for its construction).
+struct Layout {
+  int K = 0, ndisk = 0, nint = 0, ld = 0, len0 = 0, ldcb = 0;
+  std::vector<int> col_n1, col_n2, col_zlo, col_off;
+  std::vector<int> e_col, e_z;
+  std::vector<double> g2, vhalf;
+  std::vector<int> tile_idx, xact;
+  std::vector<short> pos3;
+  std::vector<int> emap, emap2, econj;  // external half-sphere index -> internal element
+  Plan1D P1, P2, P3;
+};
+
+// Build the layout; throws ApiFailure(WDF_EINVAL) on an invalid Miller set.
+Layout build_layout(const int32_t *miller, int npw_h, const int n[3], const double bvec[9]);
+Plan1D make_plan(int n);
+std::vector<int> digit_reversal(const Plan1D &P);
+
+}  // namespace wdf
+
+struct wdf_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  wdf_options opt{};
+  std::string err;
+  bool failed = false;
+
+  // system
+  int n[3] = {0, 0, 0};
+  size_t ngrid = 0;
+  double cell[9] = {0}, bvec[9] = {0}, omega = 0;
+  int npw_h = 0, nproj = 0, nocc = 0;
+  std::vector<double> dij, eps;
+  double alpha = 0;
+  double gap = 0;  // eps_{nocc+1} - eps_nocc when the library computed the ground state (else 0)
+
+  wdf::Layout lay;
+  wdf::Geo geo{};
+  wdf::FftCtx<double> f64{};
+  wdf::FftCtx<float> f32{};
+
+  // layout tables
+  wdf::DBuf t_col_off, t_col_zlo, t_e_col, t_e_z, t_tile, t_xact, t_pos3, t_g2, t_vhalf;
+  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32;
+
+  // operator data
+  wdf::DBuf vloc64, vloc32;  // V_loc on the grid
+  wdf::DBuf U64, U32;        // [nproj + nocc][ld]: projectors then occupied orbitals (internal layout)
+  wdf::DBuf lrd;             // [nproj + nocc]: D_j then alpha
+  wdf::DBuf psir64, psir32;  // [nocc][ngrid] psi_v(r) (unnormalised inverse transform)
+  wdf::DBuf kp64, kp32;      // [nocc][ld] TPA preconditioner
+  wdf::DBuf tkin;            // [nocc]
+  wdf::DBuf eps_dev;         // [nocc]
+
+  // workspaces (grow-only)
+  struct Cg {
+    wdf::DBuf r, z, p, Ap, x, cb, S, part1, part2, dbl, ints;
+  } cg64, cg32;
+  wdf::DBuf rb, rx, rr, rAx, rwork;        // refinement: b, x, r, A x (FP64), FP32 staging
+  wdf::DBuf shift, vidx_dev, thr;          // per-solve shift, orbital index, thresholds
+  wdf::DBuf gramw;                         // split partial sums of Gram products
+  wdf::DBuf xpert, dvgrid, accgrid, cb2, outi, drhoi, ext_in, ext_out, ext_out2;
+  wdf::DBuf dv_V, dv_W, dv_X, dv_AX, dv_R, dv_H, dv_Y, dv_theta, dv_jac, dv_jint, dv_small, dv_neg;
+  wdf::DBuf zeros, flag, guess, chi_out, chi_drho;
+};
+
+namespace wdf {
+
+// operators (engine.cu)
+template <typename T>
+void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const double *shift, bool with_alpha);
+
+struct SolveStats {
+  long long iters = 0;
+  int iters_max = 0;
+  int refinements = 0;
+  double max_res = 0;
+  bool converged = true;
+};
+
+// Solve (H - eps_v + alpha P) x = b for n right-hand sides in internal FP64 layout.
+void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const int *vidx_host, int n, SolveStats &ss);
+
+// chi0bar applied to npert internal vectors phi (FP64, internal layout); out and drho internal.
+void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<double> *out, cplx<double> *drho,
+                         SolveStats &ss);
+
+// generic block Davidson over internal FP64 vectors
+struct DavOp {
+  virtual ~DavOp() {}
+  virtual void apply(const cplx<double> *X, cplx<double> *Y, int n) = 0;
+  virtual bool precondition() const { return false; }
+};
+struct DavResult {
+  std::vector<double> lam;
+  std::vector<double> resnorm;
+  int iters = 0;
+  long long napply = 0;
+  bool converged = false;
+};
+// V0: n0 start vectors (internal layout, device). nwant lowest must converge; nkeep Ritz pairs
+// are carried (nkeep >= nwant). Output Ritz vectors (nkeep) are left in c->dv_X.
+DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nwant, int nkeep, int nbmax,
+                   int maxiter, double tol, bool zero_g0);
+
+void ground_state(wdf_ctx *c);     // fills U64 psi rows and c->eps
+void finish_setup(wdf_ctx *c);     // derived tables once psi and eps are known
+
+}  // namespace wdf

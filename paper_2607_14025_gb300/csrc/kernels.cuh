@@ -1,0 +1,117 @@
+// Kernel launchers of libwdf.so (internal interface between the engine and the kernels).
+#pragma once
+
+#include "common.cuh"
+
+namespace wdf {
+
+constexpr int kZCols = 16;  // rep columns per block of the n3 transforms
+
+enum { EPI_STORE = 0, EPI_HSHIFT = 1, EPI_DRHO = 2 };
+enum { OP_VLOC = 0, OP_G2R = 1, OP_PROD_R2G = 2, OP_ACCUM = 3 };
+
+// Everything an FFT launch needs for one precision.
+template <typename T> struct FftCtx {
+  Geo g;
+  Plan1D P1, P2, P3;
+  const cplx<T> *tw1, *tw2, *tw3;  // exp(2 pi i t / n) per axis
+};
+
+template <typename T> struct EpiArgs {
+  cplx<T> *Y = nullptr;         // output vectors (EPI_STORE / EPI_HSHIFT), drho (EPI_DRHO)
+  cplx<T> *Y2 = nullptr;        // EPI_DRHO: v^1/2 drho
+  const cplx<T> *X = nullptr;   // EPI_HSHIFT: the transformed vectors themselves
+  const double *shift = nullptr;  // EPI_HSHIFT: per-vector shift (eps_v)
+  const double *vhalf = nullptr;  // EPI_DRHO: v^1/2 per element
+  T scale = 1;                  // applied to the unpacked values
+};
+
+template <typename T> struct PlaneArgs {
+  cplx<T> *cb = nullptr;        // column buffer (in and out)
+  cplx<T> *cb2 = nullptr;       // OP_ACCUM output column buffer (per perturbation pair)
+  const T *field = nullptr;     // OP_VLOC: V_loc grid; OP_PROD_R2G / OP_ACCUM: psi_v(r) grids
+  cplx<T> *grid = nullptr;      // OP_G2R out; OP_PROD_R2G in (dV pairs); OP_ACCUM accumulator
+  int nocc = 0;
+};
+
+template <typename T> void set_fft_smem_limits(const Geo &g);
+template <typename T> size_t plane_smem(const Geo &g);
+template <typename T> size_t zpass_smem(const Geo &g);
+template <typename T> void launch_zpass_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st);
+template <typename T>
+void launch_zpass_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st);
+template <typename T> void launch_plane(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------
+// dense linear algebra on blocks of internal vectors (rows of length ld, nint live elements)
+
+// out[i * ldo + j] = <A_i, B_j> = sum_e w_e Re(conj(A_i[e]) B_j[e]), w = 1 on column (0,0), else 2.
+// work: scratch for split partial sums, gram_work_doubles() long (without it no split is used).
+template <typename T>
+void launch_gram(const Geo &g, const cplx<T> *A, int na, const cplx<T> *B, int nb, double *out, int ldo, double *work,
+                 size_t work_cap, cudaStream_t st);
+size_t gram_work_doubles(const Geo &g, int na, int nb, int ldo);
+// Y_s = c0 Y_s + sum_j U_j C[j * ldc + s] d_j   (d may be null: d_j = 1), s < ny, j < nu.
+template <typename T>
+void launch_lincomb(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, const double *C, int ldc,
+                    const double *d, double c0, cudaStream_t st);
+// per-vector partial inner products: part[s * nchunk + c] over element chunk c
+template <typename T>
+void launch_dot_partial(const Geo &g, const cplx<T> *A, const cplx<T> *B, int nvec, double *part, int nchunk,
+                        cudaStream_t st);
+int dot_chunks(const Geo &g);
+
+// ---------------------------------------------------------------------------------------------
+// CG state per solve (device arrays of length n unless noted)
+struct CgState {
+  double *rz, *rz_new, *pap, *rr;       // <r,z>, beta (after the scalar step), <p,Ap>, <r,r>
+  double *thr;                           // stop a solve once <r,r> <= thr
+  double *shift;                         // eps_v of each solve
+  double *part1, *part2;                 // partial sums [n * nchunk]
+  int *active;                           // 1 while the solve iterates
+  int *iters;                            // iterations done
+  int *nactive;                          // [1] count of active solves
+  int *vidx;                             // occupied orbital of each solve
+};
+
+// z = K r (TPA per orbital), p = z, and partials for <r,z>, <r,r>
+template <typename T>
+void launch_cg_start(const Geo &g, const cplx<T> *r, cplx<T> *z, cplx<T> *p, const T *kprec, const CgState &s, int n,
+                     int nchunk, cudaStream_t st);
+// alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = K r; partials <r,z>, <r,r>
+template <typename T>
+void launch_cg_update(const Geo &g, cplx<T> *x, cplx<T> *r, cplx<T> *z, const cplx<T> *p, const cplx<T> *Ap,
+                      const T *kprec, const CgState &s, int n, int nchunk, cudaStream_t st);
+// p = z + beta p for active solves
+template <typename T>
+void launch_cg_direction(const Geo &g, cplx<T> *p, const cplx<T> *z, const CgState &s, int n, cudaStream_t st);
+// reduce partials: which = 0 -> pap from part1; which = 1 -> new <r,z> from part1, rr from part2,
+// then the stopping test rr <= thr, beta and iteration counting; which = 2: rz, rr at start
+void launch_cg_scalars(const CgState &s, int n, int nchunk, int which, int maxiter, cudaStream_t st);
+
+// elementwise helpers
+template <typename T> void launch_axpby(const Geo &g, cplx<T> *y, const cplx<T> *x, int n, double a, double b, cudaStream_t st);
+template <typename T> void launch_scale_rows(const Geo &g, cplx<T> *y, const double *coef, int n, cudaStream_t st);
+template <typename Tin, typename Tout>
+void launch_convert(const Geo &g, Tout *y, const Tin *x, size_t count, cudaStream_t st);
+// external half-sphere vectors <-> internal layout
+void launch_ext_to_int(const double *ext, int n, int npw_h, const int *emap, const int *emap2, const int *econj,
+                       const double *scale_int, cplx<double> *out, int ld, cudaStream_t st);
+void launch_int_to_ext(const cplx<double> *in, int n, int ld, int npw_h, const int *emap, const int *econj,
+                       double *ext, cudaStream_t st);
+// residual subtraction for Davidson: R_a = AX_a - theta_a X_a
+void launch_ritz_residual(const Geo &g, cplx<double> *R, const cplx<double> *AX, const cplx<double> *X,
+                          const double *theta, int n, cudaStream_t st);
+// TPA preconditioner table K[v][e] = tpa(0.5 g2[e] / T_v)
+template <typename T> void launch_mul_table(const Geo &g, cplx<T> *y, const T *tab, int n, cudaStream_t st);
+template <typename T> void launch_tpa_table(const Geo &g, T *K, const double *tkin, int n, cudaStream_t st);
+void launch_kinetic(const Geo &g, const cplx<double> *X, int n, double *tkin, cudaStream_t st);
+// check for non-finite values; sets *flag = 1 if any
+template <typename T> void launch_check_finite(const T *x, size_t count, int *flag, cudaStream_t st);
+
+// symmetric eigensolver (cyclic Jacobi, parallel ordering) of an n x n matrix A (ld = n), FP64.
+// On exit w holds eigenvalues ascending and V[i * n + k] the i-th component of eigenvector k.
+void jacobi_eigh(double *A, double *V, double *w, int n, double *work, int *iwork, cudaStream_t st);
+size_t jacobi_work_doubles(int n);
+
+}  // namespace wdf

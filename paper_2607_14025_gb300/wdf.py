@@ -1,0 +1,303 @@
+"""ctypes binding of libwdf.so (include/wdf.h): argument marshalling only.
+
+Every computation happens in the library's CUDA kernels. Arrays may be torch tensors on the
+context's GPU (passed as device pointers) or numpy arrays (host memory, copied by the library).
+Complex half-sphere vectors are complex128 arrays of shape (n, npw_h). There is no CPU fallback:
+if the shared library is missing or does not load, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libwdf.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "wdf.h")
+
+WDF_OK, WDF_EINVAL, WDF_ENOMEM, WDF_ECUDA, WDF_ENOCONV, WDF_ETIMEOUT, WDF_ENAN, WDF_ESTATE = range(8)
+WDF_MEM_HOST, WDF_MEM_DEVICE = 0, 1
+WDF_FP64, WDF_MIXED = 0, 1
+WDF_PRECOND_NONE, WDF_PRECOND_TPA = 0, 1
+
+
+class WdfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"wdf error {code}: {msg}")
+        self.code = code
+
+
+class NotConverged(WdfError):
+    """An iteration hit its limit; ``result`` holds what the call produced."""
+
+    def __init__(self, code, msg, result=None):
+        super().__init__(code, msg)
+        self.result = result
+
+
+class _System(ctypes.Structure):
+    _fields_ = [
+        ("cell", ctypes.c_double * 9),
+        ("n", ctypes.c_int * 3),
+        ("npw_h", ctypes.c_int),
+        ("miller", ctypes.c_void_p),
+        ("vloc_r", ctypes.c_void_p),
+        ("nproj", ctypes.c_int),
+        ("beta", ctypes.c_void_p),
+        ("dij", ctypes.c_void_p),
+        ("nocc", ctypes.c_int),
+        ("psi", ctypes.c_void_p),
+        ("eps", ctypes.c_void_p),
+        ("mem", ctypes.c_int),
+    ]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("precond", ctypes.c_int),
+        ("cg_tol", ctypes.c_double),
+        ("cg_maxiter", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("max_batch", ctypes.c_int),
+        ("gs_tol", ctypes.c_double),
+        ("gs_maxiter", ctypes.c_int),
+        ("gs_extra", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("nsolve", ctypes.c_int64),
+        ("cg_iters", ctypes.c_int64),
+        ("cg_iters_max", ctypes.c_int32),
+        ("refinements", ctypes.c_int32),
+        ("max_residual", ctypes.c_double),
+        ("napply", ctypes.c_int64),
+        ("davidson_iters", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwdf.so (once). Raises if it is missing: the library has no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2607_14025_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "wdf_default_options": (None, [P]),
+        "wdf_setup_hamiltonian": (I, [ctypes.POINTER(P), P, P]),
+        "wdf_destroy": (None, [P]),
+        "wdf_get_orbitals": (I, [P, P, P, I]),
+        "wdf_apply_hamiltonian": (I, [P, I, P, P, I]),
+        "wdf_sternheimer": (I, [P, I, P, P, P, I, P]),
+        "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
+        "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
+        "wdf_strerror": (ctypes.c_char_p, [I]),
+        "wdf_last_error": (ctypes.c_char_p, [P]),
+        "wdf_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/wdf.h."""
+    text = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(wdf_\w+)\s*\(", text, flags=re.M)))
+
+
+# ------------------------------------------------------------------------------------------------
+# array marshalling
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_in(x, dtype, keep: list):
+    """(pointer, mem) of an input array; numpy inputs are made contiguous with the given dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+
+        want = {np.complex128: torch.complex128, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if x.dtype != want:
+            raise TypeError(f"expected a tensor of {want}, got {x.dtype}")
+        if x.is_cuda:
+            t = x.contiguous()
+            keep.append(t)
+            return t.data_ptr(), WDF_MEM_DEVICE
+        x = x.numpy()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    keep.append(a)
+    return a.ctypes.data, WDF_MEM_HOST
+
+
+class Context:
+    """One model system on one GPU (wraps wdf_setup_hamiltonian / wdf_destroy).
+
+    ``system`` needs the attributes cell (3x3), grid (n1, n2, n3), miller (npw_h x 3),
+    vloc_r (n3, n2, n1), beta (nproj x npw_h complex), dij (nproj) and nocc. When ``psi`` and
+    ``eps`` are None the library computes the occupied ground state itself.
+    """
+
+    def __init__(self, system, psi=None, eps=None, precision: str = "mixed", precond: str = "tpa", cg_tol: float = 1e-8,
+                 cg_maxiter: int = 1000, inner_tol: float = 1e-5, alpha: float = 0.0, max_batch: int = 0,
+                 gs_tol: float = 1e-10, gs_maxiter: int = 300, gs_extra: int = 8, stream: Optional[int] = None,
+                 device: int = 0, data_on_device: bool = False):
+        self._lib = load()
+        self._ctx = ctypes.c_void_p()
+        opt = _Options()
+        self._lib.wdf_default_options(ctypes.byref(opt))
+        opt.precision = {"fp64": WDF_FP64, "mixed": WDF_MIXED}[precision]
+        opt.precond = {"none": WDF_PRECOND_NONE, "tpa": WDF_PRECOND_TPA}[precond]
+        opt.cg_tol, opt.cg_maxiter, opt.inner_tol, opt.alpha = cg_tol, cg_maxiter, inner_tol, alpha
+        opt.max_batch, opt.gs_tol, opt.gs_maxiter, opt.gs_extra = max_batch, gs_tol, gs_maxiter, gs_extra
+        opt.stream = stream
+        opt.device = device
+        keep: list = []
+        s = _System()
+        s.cell[:] = [float(v) for v in np.asarray(system.cell, dtype=np.float64).reshape(9)]
+        s.n[:] = [int(v) for v in system.grid]
+        miller = np.ascontiguousarray(system.miller, dtype=np.int32)
+        keep.append(miller)
+        s.npw_h = miller.shape[0]
+        s.miller = miller.ctypes.data
+        dij = np.ascontiguousarray(system.dij, dtype=np.float64)
+        keep.append(dij)
+        s.nproj = int(np.asarray(system.beta).shape[0]) if not _is_torch(system.beta) else int(system.beta.shape[0])
+        s.dij = dij.ctypes.data if s.nproj else None
+        s.nocc = int(system.nocc)
+        vp, m1 = _ptr_in(system.vloc_r, np.float64, keep)
+        bp, m2 = _ptr_in(system.beta, np.complex128, keep) if s.nproj else (None, m1)
+        pp, m3 = _ptr_in(psi, np.complex128, keep)
+        if m3 is not None and len({m1, m2, m3}) != 1 or (m2 != m1):
+            raise ValueError("vloc_r, beta and psi must all be host arrays or all device tensors")
+        s.vloc_r, s.beta, s.psi = vp, bp, pp
+        s.mem = m1
+        e = None
+        if eps is not None:
+            e = np.ascontiguousarray(eps, dtype=np.float64)
+            keep.append(e)
+            s.eps = e.ctypes.data
+        self.npw_h = s.npw_h
+        self.nocc = s.nocc
+        self.device = device
+        rc = self._lib.wdf_setup_hamiltonian(ctypes.byref(self._ctx), ctypes.byref(s), ctypes.byref(opt))
+        self.setup_status = rc
+        if rc not in (WDF_OK, WDF_ENOCONV):
+            raise WdfError(rc, self._lib.wdf_last_error(None).decode())
+        if rc == WDF_ENOCONV:
+            self.setup_message = self._lib.wdf_last_error(self._ctx).decode()
+
+    # -- helpers ----------------------------------------------------------------------------------
+    def _check(self, rc, result=None):
+        if rc == WDF_OK:
+            return
+        msg = self._lib.wdf_last_error(self._ctx).decode()
+        if rc == WDF_ENOCONV:
+            raise NotConverged(rc, msg, result)
+        raise WdfError(rc, msg)
+
+    def _out_like(self, x, n):
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+
+            t = torch.empty((n, self.npw_h), dtype=torch.complex128, device=x.device)
+            return t, t.data_ptr()
+        a = np.empty((n, self.npw_h), dtype=np.complex128)
+        return a, a.ctypes.data
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.wdf_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points ---------------------------------------------------------------------------
+    def orbitals(self, device_tensor=None):
+        """(eps[nocc], psi[nocc, npw_h]) of the occupied ground state."""
+        eps = np.empty(self.nocc)
+        out, ptr = self._out_like(device_tensor, self.nocc)
+        mem = WDF_MEM_DEVICE if device_tensor is not None and _is_torch(device_tensor) and device_tensor.is_cuda else WDF_MEM_HOST
+        self._check(self._lib.wdf_get_orbitals(self._ctx, eps.ctypes.data, ptr, mem))
+        return eps, out
+
+    def apply_hamiltonian(self, x):
+        keep: list = []
+        x2 = x if (_is_torch(x) and x.is_cuda) else np.atleast_2d(x)
+        p, mem = _ptr_in(x2, np.complex128, keep)
+        n = x2.shape[0]
+        out, op = self._out_like(x2, n)
+        self._check(self._lib.wdf_apply_hamiltonian(self._ctx, n, p, op, mem))
+        return out
+
+    def sternheimer(self, vidx, rhs):
+        keep: list = []
+        v = np.ascontiguousarray(vidx, dtype=np.int32)
+        p, mem = _ptr_in(rhs, np.complex128, keep)
+        n = v.shape[0]
+        out, op = self._out_like(rhs, n)
+        st = Stats()
+        rc = self._lib.wdf_sternheimer(self._ctx, n, v.ctypes.data, p, op, mem, ctypes.byref(st))
+        self._check(rc, (out, st))
+        return out, st
+
+    def apply_chi0(self, phi, want_drho: bool = False):
+        """chi0bar phi; returns (out, drho or None, Stats)."""
+        keep: list = []
+        p, mem = _ptr_in(phi, np.complex128, keep)
+        n = phi.shape[0]
+        out, op = self._out_like(phi, n)
+        drho, dp = self._out_like(phi, n) if want_drho else (None, None)
+        st = Stats()
+        rc = self._lib.wdf_apply_chi0(self._ctx, n, p, op, dp, mem, ctypes.byref(st))
+        self._check(rc, (out, drho, st))
+        return out, drho, st
+
+    def pdep(self, neig: int, guess, nbasis_max: int = 0, maxiter: int = 100, tol: float = 1e-10):
+        """Lowest neig eigenpairs of chi0bar: (lambda[neig], phibar[neig, npw_h], Stats)."""
+        keep: list = []
+        p, mem = _ptr_in(guess, np.complex128, keep)
+        lam = np.empty(neig)
+        vec, vp = self._out_like(guess, neig)
+        st = Stats()
+        rc = self._lib.wdf_pdep_davidson(self._ctx, neig, nbasis_max, maxiter, tol, guess.shape[0], p, lam.ctypes.data, vp, mem,
+                                         ctypes.byref(st))
+        self._check(rc, (lam, vec, st))
+        return lam, vec, st
