@@ -171,9 +171,10 @@ def run_gpu(args):
     s = synth.make_system(WORKLOAD)
     # each rank applies chi0bar to its own seeded perturbation block (weak scaling)
     phi_h = synth.make_perturbations(s, NPERT, 1000 + rank)
+    t_setup = time.perf_counter()
     ctx = wdf.Context(s, precision=args.precision, cg_tol=1e-8, stream=stream.cuda_stream, device=local,
                       max_batch=args.max_batch)
-    gap = None
+    t_setup = time.perf_counter() - t_setup
     eps, _ = ctx.orbitals()
     phi_d = torch.from_numpy(phi_h).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -239,6 +240,8 @@ def run_gpu(args):
         "gpu_launches": None,
         "clocks": clocks,
         "peaks_source": src,
+        "setup_s": t_setup,
+        "eps_homo": float(eps[-1]),
     }
     if args.cpu_baseline:
         sys_o, R, phi1, t_gs = oracle_sample(WORKLOAD)

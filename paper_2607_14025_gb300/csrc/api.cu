@@ -269,7 +269,7 @@ struct Chi0Op : DavOp {
     agg.refinements = std::max(agg.refinements, ss.refinements);
     agg.max_res = std::max(agg.max_res, ss.max_res);
     agg.converged = agg.converged && ss.converged;
-    nsolve += (long long)2 * ((n + 1) / 2) * c->nocc;
+    nsolve += (long long)n * c->nocc;
   }
 };
 
@@ -429,7 +429,7 @@ int wdf_apply_chi0(wdf_ctx *c, int npert, const double *phi, double *out, double
       if (drho) write_out(c, c->ext_out2, c->drhoi.as<cplx<double>>(), npert, drho, mem);
       WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
     }
-    fill_stats(st, ss, (long long)2 * ((npert + 1) / 2) * c->nocc, npert, tm.ms());
+    fill_stats(st, ss, (long long)npert * c->nocc, npert, tm.ms());
     return ss.converged ? WDF_OK : WDF_ENOCONV;
   });
 }

@@ -366,6 +366,12 @@ void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<do
       gram<double>(c, psi, nocc, b, ns, w.S.as<double>(), ns);
       launch_lincomb<double>(g, b, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
     }
+    if ((npert & 1) && pp1 == npp) {
+      // the phantom partner of the last perturbation: its right-hand side is FFT rounding noise,
+      // set it to exactly zero so that its solves are skipped
+      const size_t row = sizeof(cplx<double>) * g.ld;
+      WDF_CUDA_TRY(cudaMemset2DAsync(b + ((size_t)2 * (npp - 1 - pp0) * nocc + 1) * g.ld, 2 * row, 0, row, nocc, st));
+    }
     std::vector<int> vidx(ns);
     for (int s = 0; s < ns; ++s) vidx[s] = (s / 2) % nocc;
     sternheimer_solve(c, b, x, vidx.data(), ns, sc);
