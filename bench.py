@@ -40,6 +40,8 @@ WORKLOAD = "medium"
 NPERT = 128
 NEIG = 64
 METRIC = "sternheimer_solves_per_s_at_1e-8"
+# kernel class timed for the roofline, per precision: (class, bound)
+ROOFLINE_KERNEL = {"mixed": ("plane_vloc:32", "hbm"), "fp64": ("plane_vloc:64", "hbm")}
 UNIT = "solves/s"
 
 
@@ -185,6 +187,22 @@ def run_gpu(args):
         except wdf.NotConverged as e:  # one Davidson iteration never converges all 64 pairs
             return e.result
 
+    if args.profile_step:
+        # one warm step, then exactly one step inside cudaProfilerStart/Stop (for ncu
+        # --profile-from-start off); prints a short summary and exits
+        with torch.cuda.stream(stream):
+            step(phi_d)
+            torch.cuda.synchronize(dev)
+            torch.cuda.profiler.start()
+            lam, vec, st = step(phi_d)
+            torch.cuda.synchronize(dev)
+            torch.cuda.profiler.stop()
+        print(json.dumps({"profile_step": True, "npert": NPERT, "precision": args.precision, "stats": st.as_dict()}))
+        ctx.close()
+        return
+
+    # dominant kernel of the step, timed live with CUDA events on its stream
+    target, bound = ROOFLINE_KERNEL[args.precision]
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.fill_(1.0)
@@ -196,6 +214,8 @@ def run_gpu(args):
         clk.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         stats = []
+        ctx.profile_kernel(target)
+        nl0 = wdf.launch_count()
         for i in range(args.steps):
             flush.fill_(1.0)
             ev[i][0].record(stream)
@@ -204,6 +224,9 @@ def run_gpu(args):
             stats.append(st.as_dict())
         torch.cuda.synchronize(dev)
         clocks = clk.stop()
+        launches = (wdf.launch_count() - nl0) / args.steps
+        k_launches, k_ms = ctx.profile_read()
+        ctx.profile_kernel(None)
         ms_dev = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         # end to end through the C ABI with host buffers
         torch.cuda.synchronize(dev)
@@ -224,6 +247,15 @@ def run_gpu(args):
     if rank != 0:
         return
     hbm, bf16, src = peaks()
+    # algorithmic bytes of one launch of the dominant kernel (kernels table)
+    sc = 8 if args.precision == "mixed" else 16
+    full = np.concatenate([s.miller, -s.miller[1:]])
+    ndisk = len({(int(a), int(b)) for a, b, _ in full})
+    n1, n2, n3 = s.grid
+    npair = NPERT * s.nocc // 2
+    per_launch_bytes = npair * n3 * 2 * ndisk * sc + n1 * n2 * n3 * sc // 2
+    avg_ms = k_ms / max(1, k_launches)
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if k_launches else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -237,7 +269,12 @@ def run_gpu(args):
         "max_residual": stats[-1]["max_residual"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,
                 "d2h_bytes_per_step": NEIG * s.npw_h * 16 + NEIG * 8},
-        "gpu_launches": None,
+        "gpu_launches": int(round(launches)),
+        "roofline": {"kernel": target, "bound": bound, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "launches_per_step": k_launches / args.steps, "ms_per_launch": avg_ms,
+                     "share_of_step": k_ms / args.steps / ms_dev, "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clocks,
         "peaks_source": src,
         "setup_s": t_setup,
@@ -265,7 +302,13 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--max-batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-step", action="store_true", help="one warm step, then one step between "
+                    "cudaProfilerStart/Stop for ncu --profile-from-start off; no timing line")
+    ap.add_argument("--npert", type=int, default=128, help="perturbations per block (default 128)")
     args = ap.parse_args()
+    global NPERT, NEIG
+    NPERT = args.npert
+    NEIG = min(NEIG, NPERT)
     if args.impl == "reference":
         run_reference(args)
     else:

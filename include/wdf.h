@@ -166,6 +166,23 @@ int wdf_pdep_davidson(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, doubl
                       int nguess, const double *guess, double *lambda, double *phibar, int mem,
                       wdf_stats *st);
 
+/* Instrumentation: time one kernel class with CUDA events. Every later launch of that class made
+ * by calls on ctx is bracketed by two events recorded on the stream it is launched on.
+ * kernel: a class name, optionally with ":64" or ":32" for the precision, e.g. "plane_vloc:32".
+ * Classes: zpass_g2r, zpass_r2g, plane_vloc, plane_g2r, plane_prod, plane_accum, gram, gram_sum,
+ * lincomb, dot_partial, cg_start, cg_update, cg_direction, cg_scalars, axpby, scale_rows,
+ * convert, ext_to_int, int_to_ext, ritz_residual, tpa_table, kinetic, mul_table, check_finite,
+ * jac_init, jac_rows, jac_cols, jac_check, jac_sort, split_pairs, scale_elems, gather_shift,
+ * sum_chunks. NULL stops timing. Calling it resets the counters. Errors: WDF_EINVAL. */
+int wdf_profile_kernel(wdf_ctx *ctx, const char *kernel);
+
+/* Launches of the selected class since wdf_profile_kernel and their summed device time in
+ * milliseconds. Synchronises the context's stream. */
+int wdf_profile_read(wdf_ctx *ctx, int64_t *launches, double *ms);
+
+/* Number of kernel launches the library has made in this process so far (all contexts). */
+int64_t wdf_launch_count(void);
+
 /* Static text for a status code. */
 const char *wdf_strerror(int status);
 

@@ -2,6 +2,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "engine.cuh"
@@ -12,6 +13,19 @@ namespace wdf {
 static thread_local std::string g_last_error;
 void set_error(int, const std::string &msg) { g_last_error = msg; }
 const char *last_global_error() { return g_last_error.c_str(); }
+
+thread_local Profiler *t_prof = nullptr;
+std::atomic<long long> g_launches{0};
+
+void prof_record(cudaStream_t st) {
+  Profiler *p = t_prof;
+  if (p->used == p->ev.size()) {
+    cudaEvent_t e;
+    WDF_CUDA_TRY(cudaEventCreate(&e));
+    p->ev.push_back(e);
+  }
+  WDF_CUDA_TRY(cudaEventRecord(p->ev[p->used++], st));
+}
 }  // namespace wdf
 
 namespace {
@@ -26,6 +40,10 @@ template <class F> int guarded(wdf_ctx *c, F &&body) {
     c->err = "context unusable after an earlier CUDA failure";
     return WDF_ESTATE;
   }
+  struct ProfScope {  // kernel timing applies to launches made inside this call only
+    explicit ProfScope(wdf_ctx *c) { t_prof = (c && c->prof_on) ? &c->prof : nullptr; }
+    ~ProfScope() { t_prof = nullptr; }
+  } scope(c);
   try {
     if (c) {
       cudaError_t e = cudaSetDevice(c->device);
@@ -145,6 +163,8 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   upload(c, c->t_e_z, L.e_z);
   upload(c, c->t_tile, L.tile_idx);
   upload(c, c->t_xact, L.xact);
+  upload(c, c->t_xactn, L.xactn);
+  upload(c, c->t_jidx, L.jidx);
   upload(c, c->t_pos3, L.pos3);
   upload(c, c->t_g2, L.g2);
   upload(c, c->t_vhalf, L.vhalf);
@@ -185,6 +205,8 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   g.e_z = c->t_e_z.as<int>();
   g.tile_idx = c->t_tile.as<int>();
   g.xact = c->t_xact.as<int>();
+  g.xactn = c->t_xactn.as<int>();
+  g.xmax = L.xmax;
   g.pos3 = c->t_pos3.as<short>();
   g.g2 = c->t_g2.as<double>();
   c->f64.g = g;
@@ -194,6 +216,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   c->f64.P3 = c->f32.P3 = L.P3;
   const cplx<double> *t64 = c->t_tw64.as<cplx<double>>();
   const cplx<float> *t32 = c->t_tw32.as<cplx<float>>();
+  c->f64.jidx = c->f32.jidx = (std::getenv("WDF_GENERIC_PLANE") ? nullptr : c->t_jidx.as<int>());
   c->f64.tw1 = t64;
   c->f64.tw2 = t64 + kMaxN;
   c->f64.tw3 = t64 + 2 * kMaxN;
@@ -353,8 +376,9 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->thr,       &c->gramw,     &c->xpert,   &c->dvgrid,  &c->accgrid, &c->cb2,      &c->outi,     &c->drhoi,
                   &c->ext_in,    &c->ext_out,   &c->ext_out2, &c->dv_V,   &c->dv_W,    &c->dv_X,     &c->dv_AX,    &c->dv_R,
                   &c->dv_H,      &c->dv_Y,      &c->dv_theta, &c->dv_jac, &c->dv_jint, &c->dv_small, &c->dv_neg,   &c->zeros,
-                  &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho};
+                  &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho, &c->t_xactn, &c->t_jidx};
   for (DBuf *b : bufs) b->release();
+  for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32}) {
     DBuf *cb[] = {&w->r, &w->z, &w->p, &w->Ap, &w->x, &w->cb, &w->S, &w->part1, &w->part2, &w->dbl, &w->ints};
     for (DBuf *b : cb) b->release();
@@ -459,6 +483,46 @@ int wdf_pdep_davidson(wdf_ctx *c, int neig, int nbasis_max, int maxiter, double 
     return r.converged ? WDF_OK : WDF_ENOCONV;
   });
 }
+
+int wdf_profile_kernel(wdf_ctx *c, const char *kernel) {
+  if (!c) return WDF_EINVAL;
+  return guarded(c, [&] {
+    if (c->st) WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    c->prof.used = 0;
+    c->prof.count = 0;
+    c->prof_on = kernel != nullptr;
+    if (!kernel) return WDF_OK;
+    std::string k(kernel);
+    int bits = 0;
+    const size_t colon = k.find(':');
+    if (colon != std::string::npos) {
+      bits = std::atoi(k.c_str() + colon + 1);
+      k = k.substr(0, colon);
+      if (bits != 32 && bits != 64) throw ApiFailure(WDF_EINVAL, "kernel precision suffix must be :32 or :64");
+    }
+    c->prof.target = k;
+    c->prof.bits = bits;
+    return WDF_OK;
+  });
+}
+
+int wdf_profile_read(wdf_ctx *c, int64_t *launches, double *ms) {
+  if (!c || !launches || !ms) return WDF_EINVAL;
+  return guarded(c, [&] {
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < c->prof.used; i += 2) {
+      float t = 0.f;
+      WDF_CUDA_TRY(cudaEventElapsedTime(&t, c->prof.ev[i], c->prof.ev[i + 1]));
+      tot += t;
+    }
+    *launches = c->prof.count;
+    *ms = tot;
+    return WDF_OK;
+  });
+}
+
+int64_t wdf_launch_count(void) { return (int64_t)g_launches.load(); }
 
 const char *wdf_strerror(int s) {
   switch (s) {

@@ -5,9 +5,12 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <string>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "wdf.h"
 
@@ -75,6 +78,8 @@ struct Geo {
   const int *e_z;          // [nint] n3 of each element
   const int *tile_idx;     // [ndisk] smem index pos2(i2)*pitch + pos1(i1) of each disk column
   const int *xact;         // [nxact] tile x positions (pos1) with data
+  const int *xactn;        // [nxact] the same columns in natural order (n1 mod N1)
+  int xmax;                // largest |n1| of the sphere
   const short *pos3;       // [n3] digit-reversed position along n3
   const double *g2;        // [ld] |G|^2 of each element (0 in padding)
 };
@@ -101,6 +106,37 @@ const char *last_global_error();
   } while (0)
 
 namespace wdf {
+
+// ---------------------------------------------------------------------------------------------
+// launch accounting: every kernel launch goes through launch(), which counts it and, when the
+// calling thread has selected its class for timing, records CUDA events around it on its stream
+
+struct Profiler {
+  std::string target;  // kernel class, e.g. "plane_vloc"
+  int bits = 0;        // 64, 32, or 0 for classes without a precision
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  long long count = 0;
+};
+extern thread_local Profiler *t_prof;
+extern std::atomic<long long> g_launches;
+void prof_record(cudaStream_t st);  // records the next event of t_prof
+
+template <typename T> constexpr int bits_of() { return (int)(8 * sizeof(T)); }
+
+template <typename... KArgs, typename... Args>
+inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   Args &&...args) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  const bool timed = t_prof && t_prof->bits == bits && t_prof->target == cls;
+  if (timed) prof_record(st);
+  k<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+  if (timed) {
+    prof_record(st);
+    ++t_prof->count;
+  }
+}
+
 struct CudaFailure {
   cudaError_t err;
   const char *what;

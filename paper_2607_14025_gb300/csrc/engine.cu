@@ -95,7 +95,7 @@ static void dots(wdf_ctx *c, const cplx<T> *A, const cplx<T> *B, int n, double *
   wdf_ctx::Cg &w = Prec<T>::cg(c);
   w.part1.ensure(sizeof(double) * (size_t)n * nch);
   launch_dot_partial<T>(c->geo, A, B, n, w.part1.as<double>(), nch, c->st);
-  k_sum_chunks<<<(n + 127) / 128, 128, 0, c->st>>>(w.part1.as<double>(), n, nch, out);
+  launch("sum_chunks", 0, k_sum_chunks, dim3((n + 127) / 128), dim3(128), 0, c->st, w.part1.as<double>(), n, nch, out);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -211,7 +211,7 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
   c->shift.ensure(sizeof(double) * n);
   c->thr.ensure(sizeof(double) * n);
   WDF_CUDA_TRY(cudaMemcpyAsync(c->vidx_dev.p, vidx_host, sizeof(int) * n, cudaMemcpyHostToDevice, st));
-  k_gather_shift<<<(n + 127) / 128, 128, 0, st>>>(c->vidx_dev.as<int>(), c->eps_dev.as<double>(), c->shift.as<double>(), n);
+  launch("gather_shift", 0, k_gather_shift, dim3((n + 127) / 128), dim3(128), 0, st, c->vidx_dev.as<int>(), c->eps_dev.as<double>(), c->shift.as<double>(), n);
   WDF_CUDA_TRY(cudaGetLastError());
   c->rr.ensure(vb);
   c->rAx.ensure(vb);
@@ -317,7 +317,7 @@ void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<do
   c->xpert.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
   cplx<double> *xp = c->xpert.as<cplx<double>>();
   WDF_CUDA_TRY(cudaMemsetAsync(xp, 0, sizeof(cplx<double>) * (size_t)np2 * g.ld, st));
-  k_scale_elems<<<grid_for((size_t)npert * g.ld), 256, 0, st>>>(g, xp, phi, c->t_vhalf.as<double>(), npert);
+  launch("scale_elems", 0, k_scale_elems, dim3(grid_for((size_t)npert * g.ld)), dim3(256), 0, st, g, xp, phi, c->t_vhalf.as<double>(), npert);
   WDF_CUDA_TRY(cudaGetLastError());
   // dV pairs in real space: dV_2pp + i dV_2pp+1 = ifft(x_2pp + i x_2pp+1)
   c->dvgrid.ensure(sizeof(cplx<double>) * (size_t)npp * ngrid);
@@ -622,7 +622,7 @@ void finish_setup(wdf_ctx *c) {
   pa.cb = c->cg64.cb.as<cplx<double>>();
   pa.grid = c->accgrid.as<cplx<double>>();
   launch_plane<double>(c->f64, OP_G2R, npair, pa, st);
-  k_split_pairs<double><<<grid_for((size_t)npair * c->ngrid), 256, 0, st>>>(c->accgrid.as<cplx<double>>(), npair, c->ngrid,
+  launch("split_pairs", 64, k_split_pairs<double>, dim3(grid_for((size_t)npair * c->ngrid)), dim3(256), 0, st, c->accgrid.as<cplx<double>>(), npair, c->ngrid,
                                                                            c->psir64.as<double>(), nocc);
   WDF_CUDA_TRY(cudaGetLastError());
   launch_convert<double, float>(g, c->psir32.as<float>(), c->psir64.as<double>(), (size_t)nocc * c->ngrid, st);

@@ -23,7 +23,8 @@ struct Layout {
   std::vector<int> col_n1, col_n2, col_zlo, col_off;
   std::vector<int> e_col, e_z;
   std::vector<double> g2, vhalf;
-  std::vector<int> tile_idx, xact;
+  std::vector<int> tile_idx, xact, xactn, jidx;
+  int xmax = 0;
   std::vector<short> pos3;
   std::vector<int> emap, emap2, econj;  // external half-sphere index -> internal element
   Plan1D P1, P2, P3;
@@ -59,7 +60,7 @@ struct wdf_ctx {
 
   // layout tables
   wdf::DBuf t_col_off, t_col_zlo, t_e_col, t_e_z, t_tile, t_xact, t_pos3, t_g2, t_vhalf;
-  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32;
+  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32, t_xactn, t_jidx;
 
   // operator data
   wdf::DBuf vloc64, vloc32;  // V_loc on the grid
@@ -80,6 +81,10 @@ struct wdf_ctx {
   wdf::DBuf xpert, dvgrid, accgrid, cb2, outi, drhoi, ext_in, ext_out, ext_out2;
   wdf::DBuf dv_V, dv_W, dv_X, dv_AX, dv_R, dv_H, dv_Y, dv_theta, dv_jac, dv_jint, dv_small, dv_neg;
   wdf::DBuf zeros, flag, guess, chi_out, chi_drho;
+
+  // kernel timing (wdf_profile_kernel)
+  wdf::Profiler prof;
+  bool prof_on = false;
 };
 
 namespace wdf {

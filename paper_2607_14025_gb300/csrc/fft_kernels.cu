@@ -255,13 +255,14 @@ void set_fft_smem_limits(const Geo &g) {
   WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_G2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
   WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_PROD_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
   WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
+  set_plane_fast_limits<T>(g);
 }
 
 template <typename T>
 void launch_zpass_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st) {
   if (nvec <= 0) return;
   dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
-  k_zpass_g2r<T><<<grid, kThreads, zpass_smem<T>(f.g), st>>>(X, nvec, f.g, f.P3, f.tw3, cb);
+  launch("zpass_g2r", bits_of<T>(), k_zpass_g2r<T>, dim3(grid), dim3(kThreads), zpass_smem<T>(f.g), st, X, nvec, f.g, f.P3, f.tw3, cb);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -270,22 +271,23 @@ void launch_zpass_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, 
   if (nvec <= 0) return;
   dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
   const size_t sm = zpass_smem<T>(f.g);
-  if (epi == EPI_STORE) k_zpass_r2g<T, EPI_STORE><<<grid, kThreads, sm, st>>>(cb, nvec, f.g, f.P3, f.tw3, ea);
-  else if (epi == EPI_HSHIFT) k_zpass_r2g<T, EPI_HSHIFT><<<grid, kThreads, sm, st>>>(cb, nvec, f.g, f.P3, f.tw3, ea);
-  else k_zpass_r2g<T, EPI_DRHO><<<grid, kThreads, sm, st>>>(cb, nvec, f.g, f.P3, f.tw3, ea);
+  if (epi == EPI_STORE) launch("zpass_r2g", bits_of<T>(), k_zpass_r2g<T, EPI_STORE>, dim3(grid), dim3(kThreads), sm, st, cb, nvec, f.g, f.P3, f.tw3, ea);
+  else if (epi == EPI_HSHIFT) launch("zpass_r2g", bits_of<T>(), k_zpass_r2g<T, EPI_HSHIFT>, dim3(grid), dim3(kThreads), sm, st, cb, nvec, f.g, f.P3, f.tw3, ea);
+  else launch("zpass_r2g", bits_of<T>(), k_zpass_r2g<T, EPI_DRHO>, dim3(grid), dim3(kThreads), sm, st, cb, nvec, f.g, f.P3, f.tw3, ea);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
 template <typename T>
 void launch_plane(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st) {
   if (nblk <= 0) return;
+  if (launch_plane_fast<T>(f, op, nblk, pa, st)) return;
   dim3 grid(nblk, f.g.n3);
   const size_t sm = plane_smem<T>(f.g);
   switch (op) {
-    case OP_VLOC: k_plane<T, OP_VLOC><<<grid, kThreads, sm, st>>>(f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
-    case OP_G2R: k_plane<T, OP_G2R><<<grid, kThreads, sm, st>>>(f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
-    case OP_PROD_R2G: k_plane<T, OP_PROD_R2G><<<grid, kThreads, sm, st>>>(f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
-    default: k_plane<T, OP_ACCUM><<<grid, kThreads, sm, st>>>(f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
+    case OP_VLOC: launch("plane_vloc", bits_of<T>(), k_plane<T, OP_VLOC>, dim3(grid), dim3(kThreads), sm, st, f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
+    case OP_G2R: launch("plane_g2r", bits_of<T>(), k_plane<T, OP_G2R>, dim3(grid), dim3(kThreads), sm, st, f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
+    case OP_PROD_R2G: launch("plane_prod", bits_of<T>(), k_plane<T, OP_PROD_R2G>, dim3(grid), dim3(kThreads), sm, st, f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
+    default: launch("plane_accum", bits_of<T>(), k_plane<T, OP_ACCUM>, dim3(grid), dim3(kThreads), sm, st, f.g, f.P1, f.P2, f.tw1, f.tw2, pa); break;
   }
   WDF_CUDA_TRY(cudaGetLastError());
 }

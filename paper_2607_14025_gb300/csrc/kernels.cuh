@@ -15,6 +15,7 @@ template <typename T> struct FftCtx {
   Geo g;
   Plan1D P1, P2, P3;
   const cplx<T> *tw1, *tw2, *tw3;  // exp(2 pi i t / n) per axis
+  const int *jidx;                 // [n2][n1] disk column at natural (y, x), or -1
 };
 
 template <typename T> struct EpiArgs {
@@ -35,6 +36,10 @@ template <typename T> struct PlaneArgs {
 };
 
 template <typename T> void set_fft_smem_limits(const Geo &g);
+// plane kernels specialised for compile-time sizes (plane_fast.cu); false when not available
+bool plane_fast_supported(int n1, int n2);
+template <typename T> void set_plane_fast_limits(const Geo &g);
+template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
 template <typename T> size_t plane_smem(const Geo &g);
 template <typename T> size_t zpass_smem(const Geo &g);
 template <typename T> void launch_zpass_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st);

@@ -37,48 +37,68 @@ static __device__ double block_sum(double v) {
 // ---------------------------------------------------------------------------------------------
 // Gram products out[i][j] = <A_i, B_j>
 
-constexpr int GT = 32;  // output tile
-constexpr int GK = 32;  // element chunk
+// Gram products: block tile GI x GJ = 64 x 128 outputs, 256 threads as 16 x 16, each thread a
+// 4 x 8 register tile; element chunks of GK staged k-major in shared memory so that a thread
+// reads 4 + 8 consecutive values per element (0.67 FMA per shared byte in FP32).
+constexpr int GI = 64;
+constexpr int GJ = 128;
+constexpr int GK = 16;
 
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) k_gram(Geo g, const cplx<T> *__restrict__ A, int na, const cplx<T> *__restrict__ B,
                                              int nb, double *__restrict__ out, int ldo, int echunk, size_t split_stride) {
-  __shared__ cplx<T> As[GT][GK + 1];
-  __shared__ cplx<T> Bs[GT][GK + 1];
-  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  __shared__ cplx<T> As[GK][GI];
+  __shared__ cplx<T> Bs[GK][GJ];
+  const int i0 = blockIdx.x * GI, j0 = blockIdx.y * GJ;
   const int ebeg = blockIdx.z * echunk;
   const int eend = min(g.nint, ebeg + echunk);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  Acc acc[2][2] = {{0, 0}, {0, 0}};
+  Acc acc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0;
   for (int e0 = ebeg; e0 < eend; e0 += GK) {
-    for (int t = threadIdx.x; t < GT * GK; t += 256) {
+    // 16 consecutive threads read 16 consecutive elements of one row
+#pragma unroll
+    for (int t = threadIdx.x; t < GI * GK; t += 256) {
       const int row = t / GK, col = t % GK, e = e0 + col;
-      const bool ok = e < eend;
-      const T w = (T)wgt(e, g.len0);
-      cplx<T> a = mkc<T>(0, 0), b = mkc<T>(0, 0);
-      if (ok && i0 + row < na) a = A[(size_t)(i0 + row) * g.ld + e];
-      if (ok && j0 + row < nb) b = B[(size_t)(j0 + row) * g.ld + e];
-      As[row][col] = mkc<T>(a.x * w, a.y * w);
-      Bs[row][col] = b;
+      cplx<T> a = mkc<T>(0, 0);
+      if (e < eend && i0 + row < na) {
+        a = A[(size_t)(i0 + row) * g.ld + e];
+        const T w = (T)wgt(e, g.len0);
+        a = mkc<T>(a.x * w, a.y * w);
+      }
+      As[col][row] = a;
+    }
+#pragma unroll
+    for (int t = threadIdx.x; t < GJ * GK; t += 256) {
+      const int row = t / GK, col = t % GK, e = e0 + col;
+      cplx<T> b = mkc<T>(0, 0);
+      if (e < eend && j0 + row < nb) b = B[(size_t)(j0 + row) * g.ld + e];
+      Bs[col][row] = b;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int k = 0; k < GK; ++k) {
-      const cplx<T> a0 = As[ty * 2][k], a1 = As[ty * 2 + 1][k];
-      const cplx<T> b0 = Bs[tx * 2][k], b1 = Bs[tx * 2 + 1][k];
-      acc[0][0] += (Acc)a0.x * (Acc)b0.x + (Acc)a0.y * (Acc)b0.y;
-      acc[0][1] += (Acc)a0.x * (Acc)b1.x + (Acc)a0.y * (Acc)b1.y;
-      acc[1][0] += (Acc)a1.x * (Acc)b0.x + (Acc)a1.y * (Acc)b0.y;
-      acc[1][1] += (Acc)a1.x * (Acc)b1.x + (Acc)a1.y * (Acc)b1.y;
+      cplx<T> av[4], bv[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[k][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) bv[b] = Bs[k][tx * 8 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] += (Acc)av[a].x * (Acc)bv[b].x + (Acc)av[a].y * (Acc)bv[b].y;
     }
     __syncthreads();
   }
   double *o = out + blockIdx.z * split_stride;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int i = i0 + ty * 2 + a, j = j0 + tx * 2 + b;
+    for (int b = 0; b < 8; ++b) {
+      const int i = i0 + ty * 4 + a, j = j0 + tx * 8 + b;
       if (i < na && j < nb) o[(size_t)i * ldo + j] = (double)acc[a][b];
     }
 }
@@ -94,7 +114,7 @@ __global__ void k_sum_splits(const double *__restrict__ part, int nsplit, size_t
 }
 
 static int gram_nsplit(const Geo &g, int na, int nb, int &echunk) {
-  const int tiles = ((na + GT - 1) / GT) * ((nb + GT - 1) / GT);
+  const int tiles = ((na + GI - 1) / GI) * ((nb + GJ - 1) / GJ);
   int nsplit = 1;
   const int target = 2 * 152;  // two waves of blocks on the 152 SMs
   if (tiles < target) nsplit = std::min(64, std::max(1, target / tiles));
@@ -122,14 +142,14 @@ void launch_gram(const Geo &g, const cplx<T> *A, int na, const cplx<T> *B, int n
     nsplit = 1;
     echunk = ((g.nint + GK - 1) / GK) * GK;
   }
-  dim3 grid((na + GT - 1) / GT, (nb + GT - 1) / GT, nsplit);
+  dim3 grid((na + GI - 1) / GI, (nb + GJ - 1) / GJ, nsplit);
   typedef typename std::conditional<std::is_same<T, double>::value, double, float>::type Acc;
   if (nsplit == 1) {
-    k_gram<T, Acc><<<grid, 256, 0, st>>>(g, A, na, B, nb, out, ldo, echunk, 0);
+    launch("gram", bits_of<T>(), k_gram<T, Acc>, dim3(grid), dim3(256), 0, st, g, A, na, B, nb, out, ldo, echunk, 0);
   } else {
-    k_gram<T, Acc><<<grid, 256, 0, st>>>(g, A, na, B, nb, work, ldo, echunk, stride);
+    launch("gram", bits_of<T>(), k_gram<T, Acc>, dim3(grid), dim3(256), 0, st, g, A, na, B, nb, work, ldo, echunk, stride);
     WDF_CUDA_TRY(cudaGetLastError());
-    k_sum_splits<<<(na * nb + 255) / 256, 256, 0, st>>>(work, nsplit, stride, out, na, nb, ldo);
+    launch("gram_sum", 0, k_sum_splits, dim3((na * nb + 255) / 256), dim3(256), 0, st, work, nsplit, stride, out, na, nb, ldo);
   }
   WDF_CUDA_TRY(cudaGetLastError());
 }
@@ -137,18 +157,27 @@ void launch_gram(const Geo &g, const cplx<T> *A, int na, const cplx<T> *B, int n
 // ---------------------------------------------------------------------------------------------
 // linear combinations Y_s = c0 Y_s + sum_j U_j C[j][s] d_j
 
-constexpr int LE = 64;  // elements per block
-constexpr int LS = 16;  // vectors per block
-constexpr int LJ = 32;  // coefficient rows staged at a time
+// Linear combinations: block tile LE x LS = 128 elements x 32 vectors; 256 threads, thread
+// (te = tid % 32, ts = tid / 32) accumulates elements te + 32 p (p < 4, coalesced) of vectors
+// 4 ts + q (q < 4). Rows of U and the scaled coefficients are staged LJ at a time; the
+// coefficients a warp reads are one broadcast address.
+constexpr int LE = 128;
+constexpr int LS = 32;
+template <typename T> __host__ __device__ constexpr int lj_rows() { return sizeof(T) == 8 ? 16 : 32; }  // 32 KB of U rows
 
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y, int ny, const cplx<T> *__restrict__ U, int nu,
                                                 const double *__restrict__ C, int ldc, const double *__restrict__ d, double c0) {
+  constexpr int LJ = lj_rows<T>();
   __shared__ Acc cs[LJ][LS];
-  const int e = blockIdx.x * LE + (threadIdx.x % LE);
-  const int sg = threadIdx.x / LE;  // 0..3, four vectors each
-  const int s0 = blockIdx.y * LS;
-  Acc ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+  __shared__ cplx<T> us[LJ][LE];
+  const int te = threadIdx.x % 32, ts = threadIdx.x / 32;
+  const int e0 = blockIdx.x * LE, s0 = blockIdx.y * LS;
+  Acc ax[4][4], ay[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ax[p][q] = ay[p][q] = 0;
   for (int j0 = 0; j0 < nu; j0 += LJ) {
     for (int t = threadIdx.x; t < LJ * LS; t += 256) {
       const int jj = t / LS, ss = t % LS;
@@ -157,32 +186,45 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
       if (j < nu && s < ny) v = C[(size_t)j * ldc + s] * (d ? d[j] : 1.0);
       cs[jj][ss] = (Acc)v;
     }
+    for (int t = threadIdx.x; t < LJ * LE; t += 256) {
+      const int jj = t / LE, ee = t % LE;
+      const int j = j0 + jj, e = e0 + ee;
+      us[jj][ee] = (j < nu && e < g.nint) ? U[(size_t)j * g.ld + e] : mkc<T>(0, 0);
+    }
     __syncthreads();
-    if (e < g.nint) {
-      const int jn = min(LJ, nu - j0);
-      for (int jj = 0; jj < jn; ++jj) {
-        const cplx<T> u = U[(size_t)(j0 + jj) * g.ld + e];
+    const int jn = min(LJ, nu - j0);
+    for (int jj = 0; jj < jn; ++jj) {
+      cplx<T> u[4];
+      Acc c[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const Acc c = cs[jj][sg * 4 + k];
-          ax[k] += c * (Acc)u.x;
-          ay[k] += c * (Acc)u.y;
+      for (int p = 0; p < 4; ++p) u[p] = us[jj][te + 32 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] = cs[jj][ts * 4 + q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ax[p][q] += c[q] * (Acc)u[p].x;
+          ay[p][q] += c[q] * (Acc)u[p].y;
         }
-      }
     }
     __syncthreads();
   }
-  if (e >= g.nint) return;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int s = s0 + sg * 4 + k;
+  for (int q = 0; q < 4; ++q) {
+    const int s = s0 + ts * 4 + q;
     if (s >= ny) continue;
-    cplx<T> *y = Y + (size_t)s * g.ld + e;
-    if (c0 == 0.0) {
-      *y = mkc<T>((T)ax[k], (T)ay[k]);
-    } else {
-      const cplx<T> o = *y;
-      *y = mkc<T>((T)((Acc)c0 * (Acc)o.x + ax[k]), (T)((Acc)c0 * (Acc)o.y + ay[k]));
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int e = e0 + te + 32 * p;
+      if (e >= g.nint) continue;
+      cplx<T> *y = Y + (size_t)s * g.ld + e;
+      if (c0 == 0.0) {
+        *y = mkc<T>((T)ax[p][q], (T)ay[p][q]);
+      } else {
+        const cplx<T> o = *y;
+        *y = mkc<T>((T)((Acc)c0 * (Acc)o.x + ax[p][q]), (T)((Acc)c0 * (Acc)o.y + ay[p][q]));
+      }
     }
   }
 }
@@ -193,7 +235,7 @@ void launch_lincomb(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, 
   if (ny <= 0) return;
   dim3 grid((g.nint + LE - 1) / LE, (ny + LS - 1) / LS);
   typedef typename std::conditional<std::is_same<T, double>::value, double, float>::type Acc;
-  k_lincomb<T, Acc><<<grid, 256, 0, st>>>(g, Y, ny, U, nu, C, ldc, d, c0);
+  launch("lincomb", bits_of<T>(), k_lincomb<T, Acc>, dim3(grid), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc, d, c0);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -218,7 +260,7 @@ __global__ void __launch_bounds__(256) k_dot_partial(Geo g, const cplx<T> *__res
 template <typename T>
 void launch_dot_partial(const Geo &g, const cplx<T> *A, const cplx<T> *B, int nvec, double *part, int nchunk, cudaStream_t st) {
   if (nvec <= 0) return;
-  k_dot_partial<T><<<dim3(nvec, nchunk), 256, 0, st>>>(g, A, B, part, nchunk);
+  launch("dot_partial", bits_of<T>(), k_dot_partial<T>, dim3(dim3(nvec, nchunk)), dim3(256), 0, st, g, A, B, part, nchunk);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -255,7 +297,7 @@ template <typename T>
 void launch_cg_start(const Geo &g, const cplx<T> *r, cplx<T> *z, cplx<T> *p, const T *kprec, const CgState &s, int n, int nchunk,
                      cudaStream_t st) {
   if (n <= 0) return;
-  k_cg_start<T><<<dim3(n, nchunk), 256, 0, st>>>(g, r, z, p, kprec, s, nchunk);
+  launch("cg_start", bits_of<T>(), k_cg_start<T>, dim3(dim3(n, nchunk)), dim3(256), 0, st, g, r, z, p, kprec, s, nchunk);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -299,7 +341,7 @@ template <typename T>
 void launch_cg_update(const Geo &g, cplx<T> *x, cplx<T> *r, cplx<T> *z, const cplx<T> *p, const cplx<T> *Ap, const T *kprec,
                       const CgState &s, int n, int nchunk, cudaStream_t st) {
   if (n <= 0) return;
-  k_cg_update<T><<<dim3(n, nchunk), 256, 0, st>>>(g, x, r, z, p, Ap, kprec, s, nchunk);
+  launch("cg_update", bits_of<T>(), k_cg_update<T>, dim3(dim3(n, nchunk)), dim3(256), 0, st, g, x, r, z, p, Ap, kprec, s, nchunk);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -319,7 +361,7 @@ template <typename T>
 void launch_cg_direction(const Geo &g, cplx<T> *p, const cplx<T> *z, const CgState &s, int n, cudaStream_t st) {
   if (n <= 0) return;
   const int by = std::min(64, (g.nint + 255) / 256);
-  k_cg_direction<T><<<dim3(n, by), 256, 0, st>>>(g, p, z, s, n);
+  launch("cg_direction", bits_of<T>(), k_cg_direction<T>, dim3(dim3(n, by)), dim3(256), 0, st, g, p, z, s, n);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -359,7 +401,7 @@ __global__ void k_cg_scalars(CgState s, int n, int nchunk, int which, int maxite
 
 void launch_cg_scalars(const CgState &s, int n, int nchunk, int which, int maxiter, cudaStream_t st) {
   if (n <= 0) return;
-  k_cg_scalars<<<(n + 127) / 128, 128, 0, st>>>(s, n, nchunk, which, maxiter);
+  launch("cg_scalars", 0, k_cg_scalars, dim3((n + 127) / 128), dim3(128), 0, st, s, n, nchunk, which, maxiter);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -378,7 +420,7 @@ __global__ void k_axpby(Geo g, cplx<T> *__restrict__ y, const cplx<T> *__restric
 }
 template <typename T> void launch_axpby(const Geo &g, cplx<T> *y, const cplx<T> *x, int n, double a, double b, cudaStream_t st) {
   if (n <= 0) return;
-  k_axpby<T><<<std::min(4096, (int)(((size_t)n * g.ld + 255) / 256)), 256, 0, st>>>(g, y, x, n, a, b);
+  launch("axpby", bits_of<T>(), k_axpby<T>, dim3(std::min(4096, (int)(((size_t)n * g.ld + 255) / 256))), dim3(256), 0, st, g, y, x, n, a, b);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -392,7 +434,7 @@ __global__ void k_scale_rows(Geo g, cplx<T> *__restrict__ y, const double *__res
 }
 template <typename T> void launch_scale_rows(const Geo &g, cplx<T> *y, const double *coef, int n, cudaStream_t st) {
   if (n <= 0) return;
-  k_scale_rows<T><<<std::min(4096, (int)(((size_t)n * g.ld + 255) / 256)), 256, 0, st>>>(g, y, coef, n);
+  launch("scale_rows", bits_of<T>(), k_scale_rows<T>, dim3(std::min(4096, (int)(((size_t)n * g.ld + 255) / 256))), dim3(256), 0, st, g, y, coef, n);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -402,7 +444,7 @@ __global__ void k_convert(Tout *__restrict__ y, const Tin *__restrict__ x, size_
 }
 template <typename Tin, typename Tout> void launch_convert(const Geo &, Tout *y, const Tin *x, size_t count, cudaStream_t st) {
   if (count == 0) return;
-  k_convert<Tin, Tout><<<(int)std::min<size_t>(8192, (count + 255) / 256), 256, 0, st>>>(y, x, count);
+  launch("convert", bits_of<Tout>(), k_convert<Tin, Tout>, dim3((int)std::min<size_t>(8192, (count + 255) / 256)), dim3(256), 0, st, y, x, count);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -426,7 +468,7 @@ void launch_ext_to_int(const double *ext, int n, int npw_h, const int *emap, con
                        const double *scale_int, cplx<double> *out, int ld, cudaStream_t st) {
   if (n <= 0) return;
   const size_t tot = (size_t)n * npw_h;
-  k_ext_to_int<<<(int)std::min<size_t>(8192, (tot + 255) / 256), 256, 0, st>>>(ext, n, npw_h, emap, emap2, econj, scale_int, out, ld);
+  launch("ext_to_int", 0, k_ext_to_int, dim3((int)std::min<size_t>(8192, (tot + 255) / 256)), dim3(256), 0, st, ext, n, npw_h, emap, emap2, econj, scale_int, out, ld);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -444,7 +486,7 @@ void launch_int_to_ext(const cplx<double> *in, int n, int ld, int npw_h, const i
                        cudaStream_t st) {
   if (n <= 0) return;
   const size_t tot = (size_t)n * npw_h;
-  k_int_to_ext<<<(int)std::min<size_t>(8192, (tot + 255) / 256), 256, 0, st>>>(in, n, ld, npw_h, emap, econj, ext);
+  launch("int_to_ext", 0, k_int_to_ext, dim3((int)std::min<size_t>(8192, (tot + 255) / 256)), dim3(256), 0, st, in, n, ld, npw_h, emap, econj, ext);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -460,7 +502,7 @@ __global__ void k_ritz_residual(Geo g, cplx<double> *__restrict__ R, const cplx<
 void launch_ritz_residual(const Geo &g, cplx<double> *R, const cplx<double> *AX, const cplx<double> *X, const double *theta, int n,
                           cudaStream_t st) {
   if (n <= 0) return;
-  k_ritz_residual<<<std::min(4096, (int)(((size_t)n * g.ld + 255) / 256)), 256, 0, st>>>(g, R, AX, X, theta, n);
+  launch("ritz_residual", 0, k_ritz_residual, dim3(std::min(4096, (int)(((size_t)n * g.ld + 255) / 256))), dim3(256), 0, st, g, R, AX, X, theta, n);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -481,7 +523,7 @@ __global__ void k_tpa_table(Geo g, T *__restrict__ K, const double *__restrict__
 }
 template <typename T> void launch_tpa_table(const Geo &g, T *K, const double *tkin, int n, cudaStream_t st) {
   if (n <= 0) return;
-  k_tpa_table<T><<<std::min(4096, (int)(((size_t)n * g.ld + 255) / 256)), 256, 0, st>>>(g, K, tkin, n);
+  launch("tpa_table", bits_of<T>(), k_tpa_table<T>, dim3(std::min(4096, (int)(((size_t)n * g.ld + 255) / 256))), dim3(256), 0, st, g, K, tkin, n);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -499,7 +541,7 @@ __global__ void k_kinetic(Geo g, const cplx<double> *__restrict__ X, double *__r
 }
 void launch_kinetic(const Geo &g, const cplx<double> *X, int n, double *tkin, cudaStream_t st) {
   if (n <= 0) return;
-  k_kinetic<<<n, 256, 0, st>>>(g, X, tkin);
+  launch("kinetic", 0, k_kinetic, dim3(n), dim3(256), 0, st, g, X, tkin);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -511,7 +553,7 @@ __global__ void k_mul_table(Geo g, cplx<T> *__restrict__ y, const T *__restrict_
 }
 template <typename T> void launch_mul_table(const Geo &g, cplx<T> *y, const T *tab, int n, cudaStream_t st) {
   if (n <= 0) return;
-  k_mul_table<T><<<std::min(4096, (int)(((size_t)n * g.ld + 255) / 256)), 256, 0, st>>>(g, y, tab, n);
+  launch("mul_table", bits_of<T>(), k_mul_table<T>, dim3(std::min(4096, (int)(((size_t)n * g.ld + 255) / 256))), dim3(256), 0, st, g, y, tab, n);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -522,7 +564,7 @@ __global__ void k_check_finite(const T *__restrict__ x, size_t count, int *flag)
 }
 template <typename T> void launch_check_finite(const T *x, size_t count, int *flag, cudaStream_t st) {
   if (count == 0) return;
-  k_check_finite<T><<<(int)std::min<size_t>(4096, (count + 255) / 256), 256, 0, st>>>(x, count, flag);
+  launch("check_finite", bits_of<T>(), k_check_finite<T>, dim3((int)std::min<size_t>(4096, (count + 255) / 256)), dim3(256), 0, st, x, count, flag);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -641,23 +683,23 @@ void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int 
   const int mm = std::max(2, n + (n & 1));
   double *A = work, *V = work + (size_t)mm * mm, *cs = V + (size_t)mm * mm;
   int *done = iwork;
-  k_jac_init<<<std::min(1024, (mm * mm + 255) / 256), 256, 0, st>>>(Ain, n, A, V, mm, done);
+  launch("jac_init", 0, k_jac_init, dim3(std::min(1024, (mm * mm + 255) / 256)), dim3(256), 0, st, Ain, n, A, V, mm, done);
   WDF_CUDA_TRY(cudaGetLastError());
   const int maxsweep = 40;
   int hdone = 0;
   for (int sweep = 0; sweep < maxsweep && !hdone; ++sweep) {
     for (int rd = 0; rd < mm - 1; ++rd) {
-      k_jac_rows<<<mm / 2, 128, 0, st>>>(A, mm, rd, cs, done);
-      k_jac_cols<<<mm / 2, 128, 0, st>>>(A, V, mm, rd, cs, done);
+      launch("jac_rows", 0, k_jac_rows, dim3(mm / 2), dim3(128), 0, st, A, mm, rd, cs, done);
+      launch("jac_cols", 0, k_jac_cols, dim3(mm / 2), dim3(128), 0, st, A, V, mm, rd, cs, done);
     }
-    k_jac_check<<<1, 1024, 0, st>>>(A, mm, done);
+    launch("jac_check", 0, k_jac_check, dim3(1), dim3(1024), 0, st, A, mm, done);
     WDF_CUDA_TRY(cudaGetLastError());
     if (sweep % 3 == 2) {
       WDF_CUDA_TRY(cudaMemcpyAsync(&hdone, done, sizeof(int), cudaMemcpyDeviceToHost, st));
       WDF_CUDA_TRY(cudaStreamSynchronize(st));
     }
   }
-  k_jac_sort<<<1, 256, 0, st>>>(A, V, mm, n, w, Vout);
+  launch("jac_sort", 0, k_jac_sort, dim3(1), dim3(256), 0, st, A, V, mm, n, w, Vout);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 

@@ -174,7 +174,8 @@ Layout build_layout(const int32_t *miller, int npw_h, const int n[3], const doub
   const std::vector<int> pos1 = digit_reversal(L.P1), pos2 = digit_reversal(L.P2), pos3 = digit_reversal(L.P3);
   const int pitch = n[0] + 1;
   L.tile_idx.resize(L.ndisk);
-  std::set<int> xs;
+  L.jidx.assign((size_t)n[0] * n[1], -1);
+  std::set<int> xs, xsn;
   for (int j = 0; j < L.ndisk; ++j) {
     int a, b;
     if (j < L.K) {
@@ -187,8 +188,12 @@ Layout build_layout(const int32_t *miller, int npw_h, const int n[3], const doub
     const int x = pos1[wrapi(a, n[0])], y = pos2[wrapi(b, n[1])];
     L.tile_idx[j] = y * pitch + x;
     xs.insert(x);
+    xsn.insert(wrapi(a, n[0]));
+    L.jidx[(size_t)wrapi(b, n[1]) * n[0] + wrapi(a, n[0])] = j;
+    L.xmax = std::max(L.xmax, std::abs(a));
   }
   L.xact.assign(xs.begin(), xs.end());
+  L.xactn.assign(xsn.begin(), xsn.end());
   L.pos3.resize(n[2]);
   for (int t = 0; t < n[2]; ++t) L.pos3[t] = (short)pos3[t];
   return L;

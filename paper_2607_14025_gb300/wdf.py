@@ -111,6 +111,9 @@ def load(path: str = LIB_PATH):
         "wdf_sternheimer": (I, [P, I, P, P, P, I, P]),
         "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
         "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
+        "wdf_profile_kernel": (I, [P, ctypes.c_char_p]),
+        "wdf_profile_read": (I, [P, P, P]),
+        "wdf_launch_count": (ctypes.c_int64, []),
         "wdf_strerror": (ctypes.c_char_p, [I]),
         "wdf_last_error": (ctypes.c_char_p, [P]),
         "wdf_version": (ctypes.c_char_p, []),
@@ -126,7 +129,12 @@ def load(path: str = LIB_PATH):
 def header_functions(path: str = HEADER):
     """Names of the functions declared in include/wdf.h."""
     text = open(path).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(wdf_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char \*)\s*\*?\s*(wdf_\w+)\s*\(", text, flags=re.M)))
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library in this process."""
+    return int(load().wdf_launch_count())
 
 
 # ------------------------------------------------------------------------------------------------
@@ -289,6 +297,17 @@ class Context:
         rc = self._lib.wdf_apply_chi0(self._ctx, n, p, op, dp, mem, ctypes.byref(st))
         self._check(rc, (out, drho, st))
         return out, drho, st
+
+    def profile_kernel(self, kernel):
+        """Start timing one kernel class (see include/wdf.h), or stop with None."""
+        self._check(self._lib.wdf_profile_kernel(self._ctx, kernel.encode() if kernel else None))
+
+    def profile_read(self):
+        """(launches, total ms) of the timed kernel class."""
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        self._check(self._lib.wdf_profile_read(self._ctx, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
 
     def pdep(self, neig: int, guess, nbasis_max: int = 0, maxiter: int = 100, tol: float = 1e-10):
         """Lowest neig eigenpairs of chi0bar: (lambda[neig], phibar[neig, npw_h], Stats)."""
