@@ -113,11 +113,46 @@ __global__ void k_sum_splits(const double *__restrict__ part, int nsplit, size_t
   out[(size_t)i * ldo + j] = s;
 }
 
+// Gram products with at most 8 right-hand vectors (the Gram-Schmidt steps of the Davidson
+// solver): one block per row of A computes all nb inner products; no wasted tile work.
+constexpr int kNarrow = 8;
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) k_gram_narrow(Geo g, const cplx<T> *__restrict__ A, const cplx<T> *__restrict__ B, int nb,
+                                                    double *__restrict__ out, int ldo) {
+  const int i = blockIdx.x;
+  Acc acc[kNarrow];
+#pragma unroll
+  for (int j = 0; j < kNarrow; ++j) acc[j] = 0;
+  const cplx<T> *a = A + (size_t)i * g.ld;
+  for (int e = threadIdx.x; e < g.nint; e += blockDim.x) {
+    const T w = (T)wgt(e, g.len0);
+    const cplx<T> av = a[e];
+    const Acc ax = (Acc)(av.x * w), ay = (Acc)(av.y * w);
+#pragma unroll
+    for (int j = 0; j < kNarrow; ++j)
+      if (j < nb) {
+        const cplx<T> bv = B[(size_t)j * g.ld + e];
+        acc[j] += ax * (Acc)bv.x + ay * (Acc)bv.y;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < kNarrow; ++j) {
+    if (j >= nb) break;
+    const double v = block_sum((double)acc[j]);
+    if (threadIdx.x == 0) out[(size_t)i * ldo + j] = v;
+  }
+}
+
 static int gram_nsplit(const Geo &g, int na, int nb, int &echunk) {
   const int tiles = ((na + GI - 1) / GI) * ((nb + GJ - 1) / GJ);
   int nsplit = 1;
-  const int target = 2 * 152;  // two waves of blocks on the 152 SMs
-  if (tiles < target) nsplit = std::min(64, std::max(1, target / tiles));
+  const int target = 4 * 2 * 152;  // four waves of two blocks per SM on the 152 SMs
+  if (nb <= kNarrow) {
+    echunk = g.nint;
+    return 1;
+  }
+  if (tiles < target) nsplit = std::min(64, std::max(1, (target + tiles - 1) / tiles));
   echunk = (g.nint + nsplit - 1) / nsplit;
   echunk = ((echunk + GK - 1) / GK) * GK;
   return (g.nint + echunk - 1) / echunk;
@@ -135,6 +170,12 @@ template <typename T>
 void launch_gram(const Geo &g, const cplx<T> *A, int na, const cplx<T> *B, int nb, double *out, int ldo, double *work,
                  size_t work_cap, cudaStream_t st) {
   if (na <= 0 || nb <= 0) return;
+  typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type AccN;
+  if (nb <= kNarrow) {
+    launch("gram", bits_of<T>(), k_gram_narrow<T, AccN>, dim3(na), dim3(256), 0, st, g, A, B, nb, out, ldo);
+    WDF_CUDA_TRY(cudaGetLastError());
+    return;
+  }
   int echunk;
   int nsplit = gram_nsplit(g, na, nb, echunk);
   const size_t stride = (size_t)na * ldo;
@@ -229,10 +270,50 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
   }
 }
 
+// Linear combinations into at most 8 vectors: each thread owns one element of every output.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) k_lincomb_narrow(Geo g, cplx<T> *__restrict__ Y, int ny, const cplx<T> *__restrict__ U, int nu,
+                                                       const double *__restrict__ C, int ldc, const double *__restrict__ d, double c0) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.nint) return;
+  Acc ax[kNarrow], ay[kNarrow];
+#pragma unroll
+  for (int s = 0; s < kNarrow; ++s) ax[s] = ay[s] = 0;
+  for (int j = 0; j < nu; ++j) {
+    const cplx<T> u = U[(size_t)j * g.ld + e];
+    const double dj = d ? d[j] : 1.0;
+#pragma unroll
+    for (int s = 0; s < kNarrow; ++s)
+      if (s < ny) {
+        const Acc c = (Acc)(C[(size_t)j * ldc + s] * dj);
+        ax[s] += c * (Acc)u.x;
+        ay[s] += c * (Acc)u.y;
+      }
+  }
+#pragma unroll
+  for (int s = 0; s < kNarrow; ++s) {
+    if (s >= ny) break;
+    cplx<T> *y = Y + (size_t)s * g.ld + e;
+    if (c0 == 0.0) {
+      *y = mkc<T>((T)ax[s], (T)ay[s]);
+    } else {
+      const cplx<T> o = *y;
+      *y = mkc<T>((T)((Acc)c0 * (Acc)o.x + ax[s]), (T)((Acc)c0 * (Acc)o.y + ay[s]));
+    }
+  }
+}
+
 template <typename T>
 void launch_lincomb(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, const double *C, int ldc, const double *d,
                     double c0, cudaStream_t st) {
   if (ny <= 0) return;
+  if (ny <= kNarrow) {
+    typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type AccN;
+    launch("lincomb", bits_of<T>(), k_lincomb_narrow<T, AccN>, dim3((g.nint + 255) / 256), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc,
+           d, c0);
+    WDF_CUDA_TRY(cudaGetLastError());
+    return;
+  }
   dim3 grid((g.nint + LE - 1) / LE, (ny + LS - 1) / LS);
   typedef typename std::conditional<std::is_same<T, double>::value, double, float>::type Acc;
   launch("lincomb", bits_of<T>(), k_lincomb<T, Acc>, dim3(grid), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc, d, c0);
