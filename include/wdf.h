@@ -166,6 +166,24 @@ int wdf_pdep_davidson(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, doubl
                       int nguess, const double *guess, double *lambda, double *phibar, int mem,
                       wdf_stats *st);
 
+/* Bytes of the device array behind wdf_apply_hamiltonian_noalloc: 64 MiB, present on every GPU
+ * that loads the library for the life of the process. */
+#define WDF_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* H x for nvec vectors, the same result as wdf_apply_hamiltonian, without allocating any device
+ * memory. For callers that cannot call cudaMalloc: code running inside someone else's CUDA graph
+ * capture, processes whose device memory is owned by another allocator (a framework's caching
+ * pool), or services with a fixed memory budget. The paper has no counterpart: this entry point
+ * only changes where the temporaries live. All of them come from one file-scope device array of
+ * WDF_NOALLOC_SCRATCH_BYTES; a call that would need more (about 0.7 MB per vector for a 64^3 grid
+ * with 8,440 plane waves) returns WDF_EINVAL and asks for fewer vectors per call.
+ * in, out: [nvec][npw_h] complex in DEVICE memory of the context's GPU; out may not alias in.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it, so make that first call before any stream capture. Every call on a device shares
+ * the array: calls whose GPU work may overlap (different streams without ordering) race.
+ * Errors: WDF_EINVAL, WDF_ECUDA, WDF_ESTATE. */
+int wdf_apply_hamiltonian_noalloc(wdf_ctx *ctx, int nvec, const double *in, double *out);
+
 /* Instrumentation: time one kernel class with CUDA events. Every later launch of that class made
  * by calls on ctx is bracketed by two events recorded on the stream it is launched on.
  * kernel: a class name, optionally with ":64" or ":32" for the precision, e.g. "plane_vloc:32".

@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "wdf_sternheimer": (I, [P, I, P, P, P, I, P]),
         "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
         "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
+        "wdf_apply_hamiltonian_noalloc": (I, [P, I, P, P]),
         "wdf_profile_kernel": (I, [P, ctypes.c_char_p]),
         "wdf_profile_read": (I, [P, P, P]),
         "wdf_launch_count": (ctypes.c_int64, []),
@@ -273,6 +274,22 @@ class Context:
         n = x2.shape[0]
         out, op = self._out_like(x2, n)
         self._check(self._lib.wdf_apply_hamiltonian(self._ctx, n, p, op, mem))
+        return out
+
+    def apply_hamiltonian_noalloc(self, x, out):
+        """H x into ``out`` without any device allocation by the library.
+
+        For callers that cannot allocate GPU memory (inside another component's graph capture,
+        or under an allocator that owns the device): x and out are complex128 CUDA tensors of
+        shape (nvec, npw_h) that the caller owns; the library's temporaries live in a fixed
+        64 MiB device array. The first call on a device must come before any stream capture.
+        """
+        if not (_is_torch(x) and x.is_cuda and _is_torch(out) and out.is_cuda):
+            raise TypeError("apply_hamiltonian_noalloc takes CUDA tensors for x and out")
+        xs = x.contiguous()
+        if not out.is_contiguous() or out.shape != xs.shape or out.dtype != xs.dtype:
+            raise ValueError("out must be a contiguous tensor shaped like x")
+        self._check(self._lib.wdf_apply_hamiltonian_noalloc(self._ctx, xs.shape[0], xs.data_ptr(), out.data_ptr()))
         return out
 
     def sternheimer(self, vidx, rhs):
