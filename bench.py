@@ -41,7 +41,7 @@ NPERT = 128
 NEIG = 64
 METRIC = "sternheimer_solves_per_s_at_1e-8"
 # kernel class timed for the roofline, per precision: (class, bound)
-ROOFLINE_KERNEL = {"mixed": ("plane_vloc:32", "hbm"), "fp64": ("plane_vloc:64", "hbm")}
+ROOFLINE_KERNEL = {"mixed_df": ("plane_vloc:32", "hbm"), "mixed": ("plane_vloc:32", "hbm"), "fp64": ("plane_vloc:64", "hbm")}
 UNIT = "solves/s"
 
 
@@ -248,7 +248,7 @@ def run_gpu(args):
         return
     hbm, bf16, src = peaks()
     # algorithmic bytes of one launch of the dominant kernel (kernels table)
-    sc = 8 if args.precision == "mixed" else 16
+    sc = 16 if args.precision == "fp64" else 8
     full = np.concatenate([s.miller, -s.miller[1:]])
     ndisk = len({(int(a), int(b)) for a, b, _ in full})
     n1, n2, n3 = s.grid
@@ -259,7 +259,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "dtype": {"mixed": "f32+f64", "mixed_df": "f32+df64+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": "medium: L=20 bohr, 64^3 grid, |G|^2<=25, 8440 stored PWs, 32 atoms (128 KB projectors), "
                                "64 occupied, 128 perturbations per GPU, PDEP 64 eigenpairs, one Davidson iteration per step",
                    "precision": args.precision, "cg_tol": 1e-8, "l2": "flushed (256 MiB write) before each step; working set > L2",
@@ -299,7 +299,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["wdf", "reference"], default="wdf")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed_df", "mixed", "fp64"], default="mixed")
     ap.add_argument("--max-batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true", help="one warm step, then one step between "

@@ -54,9 +54,14 @@ enum wdf_mem { WDF_MEM_HOST = 0, WDF_MEM_DEVICE = 1 };
 /* Arithmetic of the Sternheimer solves.
  * WDF_FP64: every FFT, product, projection and CG update in FP64.
  * WDF_MIXED: inner conjugate-gradient iterations in FP32 (FFTs, H application, projections);
- *   the residual b - A x, the accumulated solution, the density response and the Davidson linear
- *   algebra in FP64 (iterative refinement), so the stopping test is an FP64 residual. */
-enum wdf_precision { WDF_FP64 = 0, WDF_MIXED = 1 };
+ *   the residual b - A x, the accumulated solution, the right-hand sides, the density response
+ *   and the Davidson linear algebra in FP64 (iterative refinement), so the stopping test is an
+ *   FP64 residual.
+ * WDF_MIXED_DF: as WDF_MIXED, but the FFTs and projections of the residuals, right-hand sides and
+ *   density response run in double-float arithmetic (pairs of FP32 numbers, about 48 significant
+ *   bits, relative error near 1e-14) on the FP32 units; vectors, sums and the Davidson algebra
+ *   stay FP64. GB300 issues FP32 about 60 times faster than FP64. */
+enum wdf_precision { WDF_FP64 = 0, WDF_MIXED = 1, WDF_MIXED_DF = 2 };
 
 enum wdf_precond { WDF_PRECOND_NONE = 0, WDF_PRECOND_TPA = 1 };
 
@@ -186,8 +191,8 @@ int wdf_apply_hamiltonian_noalloc(wdf_ctx *ctx, int nvec, const double *in, doub
 
 /* Instrumentation: time one kernel class with CUDA events. Every later launch of that class made
  * by calls on ctx is bracketed by two events recorded on the stream it is launched on.
- * kernel: a class name, optionally with ":64" or ":32" for the precision, e.g. "plane_vloc:32".
- * Classes: zpass_g2r, zpass_r2g, plane_vloc, plane_g2r, plane_prod, plane_accum, gram, gram_sum,
+ * kernel: a class name, optionally with ":64", ":32" or ":48" for the precision, e.g. "plane_vloc:32".
+ * Precision suffixes: 64 (FP64), 32 (FP32), 48 (double-float). Classes: zpass_g2r, zpass_r2g, plane_vloc, plane_g2r, plane_prod, plane_accum, gram, gram_sum,
  * lincomb, dot_partial, cg_start, cg_update, cg_direction, cg_scalars, axpby, scale_rows,
  * convert, ext_to_int, int_to_ext, ritz_residual, tpa_table, kinetic, mul_table, check_finite,
  * jac_init, jac_rows, jac_cols, jac_check, jac_sort, split_pairs, scale_elems, gather_shift,

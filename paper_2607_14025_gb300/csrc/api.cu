@@ -186,6 +186,11 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   }
   upload(c, c->t_tw64, tw64);
   upload(c, c->t_tw32, tw32);
+  {
+    std::vector<df64> twdf(tw64.size());
+    for (size_t i = 0; i < tw64.size(); ++i) twdf[i] = df64(tw64[i]);
+    upload(c, c->t_twdf, twdf);
+  }
 
   Geo &g = c->geo;
   g.n1 = sys->n[0];
@@ -216,7 +221,17 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   c->f64.P3 = c->f32.P3 = L.P3;
   const cplx<double> *t64 = c->t_tw64.as<cplx<double>>();
   const cplx<float> *t32 = c->t_tw32.as<cplx<float>>();
-  c->f64.jidx = c->f32.jidx = (std::getenv("WDF_GENERIC_PLANE") ? nullptr : c->t_jidx.as<int>());
+  c->fdf.g = g;
+  c->fdf.P1 = L.P1;
+  c->fdf.P2 = L.P2;
+  c->fdf.P3 = L.P3;
+  {
+    const cplx<df64> *tdf = c->t_twdf.as<cplx<df64>>();
+    c->fdf.tw1 = tdf;
+    c->fdf.tw2 = tdf + kMaxN;
+    c->fdf.tw3 = tdf + 2 * kMaxN;
+  }
+  c->f64.jidx = c->f32.jidx = c->fdf.jidx = (std::getenv("WDF_GENERIC_PLANE") ? nullptr : c->t_jidx.as<int>());
   c->f64.tw1 = t64;
   c->f64.tw2 = t64 + kMaxN;
   c->f64.tw3 = t64 + 2 * kMaxN;
@@ -227,6 +242,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
     throw ApiFailure(WDF_EINVAL, "FFT plane does not fit in shared memory in FP64 (n1 * n2 too large)");
   set_fft_smem_limits<double>(g);
   set_fft_smem_limits<float>(g);
+  set_fft_smem_limits<df64>(g);
 
   // local potential
   c->vloc64.ensure(sizeof(double) * c->ngrid);
@@ -341,7 +357,7 @@ int wdf_setup_hamiltonian(wdf_ctx **out, const wdf_system *sys, const wdf_option
     set_error(WDF_EINVAL, "device ordinal out of range");
     return WDF_EINVAL;
   }
-  if ((c->opt.precision != WDF_FP64 && c->opt.precision != WDF_MIXED) ||
+  if ((c->opt.precision != WDF_FP64 && c->opt.precision != WDF_MIXED && c->opt.precision != WDF_MIXED_DF) ||
       (c->opt.precond != WDF_PRECOND_NONE && c->opt.precond != WDF_PRECOND_TPA) || !(c->opt.cg_tol > 0) ||
       c->opt.cg_maxiter < 1 || !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1) || !(c->opt.gs_tol > 0) || c->opt.gs_maxiter < 1 ||
       c->opt.max_batch < 0 || c->opt.gs_extra < 0) {
@@ -376,10 +392,12 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->thr,       &c->gramw,     &c->xpert,   &c->dvgrid,  &c->accgrid, &c->cb2,      &c->outi,     &c->drhoi,
                   &c->ext_in,    &c->ext_out,   &c->ext_out2, &c->dv_V,   &c->dv_W,    &c->dv_X,     &c->dv_AX,    &c->dv_R,
                   &c->dv_H,      &c->dv_Y,      &c->dv_theta, &c->dv_jac, &c->dv_jint, &c->dv_small, &c->dv_neg,   &c->zeros,
-                  &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho, &c->t_xactn, &c->t_jidx};
+                  &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho, &c->t_xactn, &c->t_jidx,
+                  &c->t_twdf,    &c->vlocdf,    &c->Udf,     &c->psirdf,   &c->dfa,     &c->dfb,
+                  &c->xpdf,      &c->dvgriddf,  &c->accgriddf, &c->cb2df,  &c->drdf,    &c->oudf};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
-  for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32}) {
+  for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {
     DBuf *cb[] = {&w->r, &w->z, &w->p, &w->Ap, &w->x, &w->cb, &w->S, &w->part1, &w->part2, &w->dbl, &w->ints};
     for (DBuf *b : cb) b->release();
   }
@@ -498,7 +516,7 @@ int wdf_profile_kernel(wdf_ctx *c, const char *kernel) {
     if (colon != std::string::npos) {
       bits = std::atoi(k.c_str() + colon + 1);
       k = k.substr(0, colon);
-      if (bits != 32 && bits != 64) throw ApiFailure(WDF_EINVAL, "kernel precision suffix must be :32 or :64");
+      if (bits != 32 && bits != 64 && bits != 48) throw ApiFailure(WDF_EINVAL, "kernel precision suffix must be :32, :48 or :64");
     }
     c->prof.target = k;
     c->prof.bits = bits;

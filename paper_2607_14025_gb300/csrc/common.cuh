@@ -12,6 +12,7 @@
 #include <utility>
 #include <vector>
 
+#include "df64.cuh"
 #include "wdf.h"
 
 namespace wdf {
@@ -22,6 +23,10 @@ namespace wdf {
 template <typename T> struct cplx_t;
 template <> struct cplx_t<double> { typedef double2 type; };
 template <> struct cplx_t<float> { typedef float2 type; };
+struct __align__(16) cdf64 {
+  df64 x, y;
+};
+template <> struct cplx_t<df64> { typedef cdf64 type; };
 template <typename T> using cplx = typename cplx_t<T>::type;
 
 template <typename T> __host__ __device__ __forceinline__ cplx<T> mkc(T a, T b) {
@@ -122,7 +127,8 @@ extern thread_local Profiler *t_prof;
 extern std::atomic<long long> g_launches;
 void prof_record(cudaStream_t st);  // records the next event of t_prof
 
-template <typename T> constexpr int bits_of() { return (int)(8 * sizeof(T)); }
+// precision tag of a kernel instance: 64 (FP64), 32 (FP32), 48 (double-float)
+template <typename T> constexpr int bits_of() { return std::is_same<T, df64>::value ? 48 : (int)(8 * sizeof(T)); }
 
 template <typename... KArgs, typename... Args>
 inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -65,6 +65,35 @@ template <> struct Prec<float> {
   static const float *kp(wdf_ctx *c) { return c->kp32.as<float>(); }
   static wdf_ctx::Cg &cg(wdf_ctx *c) { return c->cg32; }
 };
+template <> struct Prec<df64> {
+  static const FftCtx<df64> &f(wdf_ctx *c) { return c->fdf; }
+  static const df64 *vloc(wdf_ctx *c) { return c->vlocdf.as<df64>(); }
+  static const cplx<df64> *U(wdf_ctx *c) { return c->Udf.as<cplx<df64>>(); }
+  static wdf_ctx::Cg &cg(wdf_ctx *c) { return c->cgdf; }
+};
+
+// buffers of the right-hand-side / density-response stage in FP64 or double-float
+template <typename R> struct Stage;
+template <> struct Stage<double> {
+  static const double *psir(wdf_ctx *c) { return c->psir64.as<double>(); }
+  static DBuf &dv(wdf_ctx *c) { return c->dvgrid; }
+  static DBuf &acc(wdf_ctx *c) { return c->accgrid; }
+  static DBuf &cb2(wdf_ctx *c) { return c->cb2; }
+};
+template <> struct Stage<df64> {
+  static const df64 *psir(wdf_ctx *c) { return c->psirdf.as<df64>(); }
+  static DBuf &dv(wdf_ctx *c) { return c->dvgriddf; }
+  static DBuf &acc(wdf_ctx *c) { return c->accgriddf; }
+  static DBuf &cb2(wdf_ctx *c) { return c->cb2df; }
+};
+
+// FP64 complex vectors <-> double-float complex vectors (n rows of ld)
+static void to_df(wdf_ctx *c, cplx<df64> *y, const cplx<double> *x, size_t nrows) {
+  launch_convert<double, df64>(c->geo, (df64 *)y, (const double *)x, 2 * nrows * c->geo.ld, c->st);
+}
+static void from_df(wdf_ctx *c, cplx<double> *y, const cplx<df64> *x, size_t nrows) {
+  launch_convert<df64, double>(c->geo, (double *)y, (const df64 *)x, 2 * nrows * c->geo.ld, c->st);
+}
 
 static const double *zeros(wdf_ctx *c, size_t n) {
   if (c->zeros.cap < n * sizeof(double)) {
@@ -205,7 +234,7 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
   if (n <= 0) return;
   const Geo &g = c->geo;
   cudaStream_t st = c->st;
-  const bool mixed = c->opt.precision == WDF_MIXED;
+  const bool mixed = c->opt.precision != WDF_FP64;  // FP32 inner solves (WDF_MIXED, WDF_MIXED_DF)
   const size_t vb = sizeof(cplx<double>) * (size_t)n * g.ld;
   c->vidx_dev.ensure(sizeof(int) * n);
   c->shift.ensure(sizeof(double) * n);
@@ -286,8 +315,16 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
       launch_axpby<double>(g, x, d, n, 1.0, 1.0, st);
     }
     for (int s = 0; s < n; ++s) iters_total[s] += it[s];
-    // r = b - A x in FP64
-    apply_operator<double>(c, x, Ax, n, c->shift.as<double>(), true);
+    // r = b - A x; A x in FP64, or in double-float (FP64 vectors converted in and out)
+    if (c->opt.precision == WDF_MIXED_DF) {
+      c->dfa.ensure(vb);
+      c->dfb.ensure(vb);
+      to_df(c, c->dfa.as<cplx<df64>>(), x, n);
+      apply_operator<df64>(c, c->dfa.as<cplx<df64>>(), c->dfb.as<cplx<df64>>(), n, c->shift.as<double>(), true);
+      from_df(c, Ax, c->dfb.as<cplx<df64>>(), n);
+    } else {
+      apply_operator<double>(c, x, Ax, n, c->shift.as<double>(), true);
+    }
     WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
     launch_axpby<double>(g, r, Ax, n, -1.0, 1.0, st);
   }
@@ -305,41 +342,55 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
 // ---------------------------------------------------------------------------------------------
 // chi0bar by DFPT (paper Sec. 2.1). phi: npert internal FP64 vectors (G = 0 ignored).
 
-void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<double> *out, cplx<double> *drho,
-                         SolveStats &ss) {
+// Stages S2, S3, S7, S8 in R (FP64 or double-float); xp: np2 rows of v^1/2 phi (FP64). Results
+// (np2 rows, FP64) go to ou = v^1/2 drho and dr = drho.
+template <typename R>
+static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, cplx<double> *ou, cplx<double> *dr, SolveStats &ss) {
+  constexpr bool DF = std::is_same<R, df64>::value;
   const Geo &g = c->geo;
   cudaStream_t st = c->st;
-  const FftCtx<double> &f = c->f64;
+  const FftCtx<R> &f = Prec<R>::f(c);
+  wdf_ctx::Cg &w = Prec<R>::cg(c);
   const int npp = (npert + 1) / 2, np2 = 2 * npp, nocc = c->nocc;
   const size_t ngrid = c->ngrid;
   const size_t cbpair = (size_t)g.n3 * g.ldcb;
-  // x = v^1/2 phi (extra zero row when npert is odd)
-  c->xpert.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
-  cplx<double> *xp = c->xpert.as<cplx<double>>();
-  WDF_CUDA_TRY(cudaMemsetAsync(xp, 0, sizeof(cplx<double>) * (size_t)np2 * g.ld, st));
-  launch("scale_elems", 0, k_scale_elems, dim3(grid_for((size_t)npert * g.ld)), dim3(256), 0, st, g, xp, phi, c->t_vhalf.as<double>(), npert);
-  WDF_CUDA_TRY(cudaGetLastError());
+  const size_t rowb = sizeof(cplx<R>) * g.ld;
+  const cplx<R> *xp;
+  if constexpr (DF) {
+    c->xpdf.ensure(rowb * np2);
+    to_df(c, c->xpdf.as<cplx<df64>>(), xp64, np2);
+    xp = c->xpdf.as<cplx<R>>();
+  } else {
+    xp = xp64;
+  }
   // dV pairs in real space: dV_2pp + i dV_2pp+1 = ifft(x_2pp + i x_2pp+1)
-  c->dvgrid.ensure(sizeof(cplx<double>) * (size_t)npp * ngrid);
-  cplx<double> *dv = c->dvgrid.as<cplx<double>>();
+  DBuf &dvb = Stage<R>::dv(c);
+  dvb.ensure(sizeof(cplx<R>) * (size_t)npp * ngrid);
+  cplx<R> *dv = dvb.as<cplx<R>>();
   {
-    auto &w = c->cg64;
-    w.cb.ensure(sizeof(cplx<double>) * (size_t)npp * cbpair);
-    launch_zpass_g2r<double>(f, xp, np2, w.cb.as<cplx<double>>(), st);
-    PlaneArgs<double> pa;
-    pa.cb = w.cb.as<cplx<double>>();
+    w.cb.ensure(sizeof(cplx<R>) * (size_t)npp * cbpair);
+    launch_zpass_g2r<R>(f, xp, np2, w.cb.as<cplx<R>>(), st);
+    PlaneArgs<R> pa;
+    pa.cb = w.cb.as<cplx<R>>();
     pa.grid = dv;
-    launch_plane<double>(f, OP_G2R, npp, pa, st);
+    launch_plane<R>(f, OP_G2R, npp, pa, st);
+  }
+  cplx<R> *drR, *ouR;
+  if constexpr (DF) {
+    c->drdf.ensure(rowb * np2);
+    c->oudf.ensure(rowb * np2);
+    drR = c->drdf.as<cplx<R>>();
+    ouR = c->oudf.as<cplx<R>>();
+  } else {
+    drR = dr;
+    ouR = ou;
   }
   // perturbation pairs per chunk so that at most max_batch solves are resident
   int cpp = npp;
   if (c->opt.max_batch > 0) cpp = std::max(1, std::min(npp, c->opt.max_batch / (2 * nocc)));
-  // results go to scratch with an even number of rows (the last pair may hold a phantom row)
-  c->chi_out.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
-  c->chi_drho.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
-  cplx<double> *dr = c->chi_drho.as<cplx<double>>(), *ou = c->chi_out.as<cplx<double>>();
   ss = SolveStats();
   SolveStats sc;
+  const cplx<R> *psi = Prec<R>::U(c) + (size_t)c->nproj * g.ld;
   for (int pp0 = 0; pp0 < npp; pp0 += cpp) {
     const int pp1 = std::min(npp, pp0 + cpp);
     const int nq = (pp1 - pp0) * nocc, ns = 2 * nq;
@@ -347,24 +398,30 @@ void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<do
     c->rb.ensure(sizeof(cplx<double>) * (size_t)ns * g.ld);
     c->rx.ensure(sizeof(cplx<double>) * (size_t)ns * g.ld);
     cplx<double> *b = c->rb.as<cplx<double>>(), *x = c->rx.as<cplx<double>>();
-    auto &w = c->cg64;
-    w.cb.ensure(sizeof(cplx<double>) * (size_t)nq * cbpair);
-    cplx<double> *cb = w.cb.as<cplx<double>>();
+    cplx<R> *bR;
+    if constexpr (DF) {
+      c->dfa.ensure(rowb * ns);
+      bR = c->dfa.as<cplx<R>>();
+    } else {
+      bR = b;
+    }
+    w.cb.ensure(sizeof(cplx<R>) * (size_t)nq * cbpair);
+    cplx<R> *cb = w.cb.as<cplx<R>>();
     {
-      PlaneArgs<double> pa;
+      PlaneArgs<R> pa;
       pa.cb = cb;
-      pa.field = c->psir64.as<double>();
+      pa.field = Stage<R>::psir(c);
       pa.grid = dv + (size_t)pp0 * ngrid;
       pa.nocc = nocc;
-      launch_plane<double>(f, OP_PROD_R2G, nq, pa, st);
-      EpiArgs<double> ea;
-      ea.Y = b;
-      ea.scale = 1.0 / (double)ngrid;
-      launch_zpass_r2g<double>(f, EPI_STORE, cb, ns, ea, st);
-      const cplx<double> *psi = c->U64.as<cplx<double>>() + (size_t)c->nproj * g.ld;
+      launch_plane<R>(f, OP_PROD_R2G, nq, pa, st);
+      EpiArgs<R> ea;
+      ea.Y = bR;
+      ea.scale = R(1.0 / (double)ngrid);
+      launch_zpass_r2g<R>(f, EPI_STORE, cb, ns, ea, st);
       w.S.ensure(sizeof(double) * (size_t)nocc * ns);
-      gram<double>(c, psi, nocc, b, ns, w.S.as<double>(), ns);
-      launch_lincomb<double>(g, b, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
+      gram<R>(c, psi, nocc, bR, ns, w.S.as<double>(), ns);
+      launch_lincomb<R>(g, bR, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
+      if constexpr (DF) from_df(c, b, bR, ns);
     }
     if ((npert & 1) && pp1 == npp) {
       // the phantom partner of the last perturbation: its right-hand side is FFT rounding noise,
@@ -381,25 +438,58 @@ void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<do
     ss.max_res = std::max(ss.max_res, sc.max_res);
     ss.converged = ss.converged && sc.converged;
     // drho_p = (4/Omega) fft_n(sum_v psi_v ifft(dpsi_vp)); out = v^1/2 drho
-    w.cb.ensure(sizeof(cplx<double>) * (size_t)nq * cbpair);
-    cb = w.cb.as<cplx<double>>();
-    c->cb2.ensure(sizeof(cplx<double>) * (size_t)(pp1 - pp0) * cbpair);
-    c->accgrid.ensure(sizeof(cplx<double>) * (size_t)(pp1 - pp0) * ngrid);
-    launch_zpass_g2r<double>(f, x, ns, cb, st);
-    PlaneArgs<double> pa;
+    const cplx<R> *xR;
+    if constexpr (DF) {
+      c->dfb.ensure(rowb * ns);
+      to_df(c, c->dfb.as<cplx<df64>>(), x, ns);
+      xR = c->dfb.as<cplx<R>>();
+    } else {
+      xR = x;
+    }
+    w.cb.ensure(sizeof(cplx<R>) * (size_t)nq * cbpair);
+    cb = w.cb.as<cplx<R>>();
+    DBuf &cb2 = Stage<R>::cb2(c), &accb = Stage<R>::acc(c);
+    cb2.ensure(sizeof(cplx<R>) * (size_t)(pp1 - pp0) * cbpair);
+    accb.ensure(sizeof(cplx<R>) * (size_t)(pp1 - pp0) * ngrid);
+    launch_zpass_g2r<R>(f, xR, ns, cb, st);
+    PlaneArgs<R> pa;
     pa.cb = cb;
-    pa.cb2 = c->cb2.as<cplx<double>>();
-    pa.field = c->psir64.as<double>();
-    pa.grid = c->accgrid.as<cplx<double>>();
+    pa.cb2 = cb2.as<cplx<R>>();
+    pa.field = Stage<R>::psir(c);
+    pa.grid = accb.as<cplx<R>>();
     pa.nocc = nocc;
-    launch_plane<double>(f, OP_ACCUM, pp1 - pp0, pa, st);
-    EpiArgs<double> ea;
-    ea.Y = dr + (size_t)(2 * pp0) * g.ld;
-    ea.Y2 = ou + (size_t)(2 * pp0) * g.ld;
+    launch_plane<R>(f, OP_ACCUM, pp1 - pp0, pa, st);
+    EpiArgs<R> ea;
+    ea.Y = drR + (size_t)(2 * pp0) * g.ld;
+    ea.Y2 = ouR + (size_t)(2 * pp0) * g.ld;
     ea.vhalf = c->t_vhalf.as<double>();
-    ea.scale = 4.0 / (c->omega * (double)ngrid);
-    launch_zpass_r2g<double>(f, EPI_DRHO, c->cb2.as<cplx<double>>(), 2 * (pp1 - pp0), ea, st);
+    ea.scale = R(4.0 / (c->omega * (double)ngrid));
+    launch_zpass_r2g<R>(f, EPI_DRHO, cb2.as<cplx<R>>(), 2 * (pp1 - pp0), ea, st);
   }
+  if constexpr (DF) {
+    from_df(c, dr, drR, np2);
+    from_df(c, ou, ouR, np2);
+  }
+}
+
+void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<double> *out, cplx<double> *drho,
+                         SolveStats &ss) {
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  const int npp = (npert + 1) / 2, np2 = 2 * npp;
+  // x = v^1/2 phi (extra zero row when npert is odd)
+  c->xpert.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+  cplx<double> *xp = c->xpert.as<cplx<double>>();
+  WDF_CUDA_TRY(cudaMemsetAsync(xp, 0, sizeof(cplx<double>) * (size_t)np2 * g.ld, st));
+  launch("scale_elems", 0, k_scale_elems, dim3(grid_for((size_t)npert * g.ld)), dim3(256), 0, st, g, xp, phi,
+         c->t_vhalf.as<double>(), npert);
+  WDF_CUDA_TRY(cudaGetLastError());
+  // results go to scratch with an even number of rows (the last pair may hold a phantom row)
+  c->chi_out.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+  c->chi_drho.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+  cplx<double> *dr = c->chi_drho.as<cplx<double>>(), *ou = c->chi_out.as<cplx<double>>();
+  if (c->opt.precision == WDF_MIXED_DF) chi0_stages<df64>(c, xp, npert, ou, dr, ss);
+  else chi0_stages<double>(c, xp, npert, ou, dr, ss);
   const size_t nb = sizeof(cplx<double>) * (size_t)npert * g.ld;
   WDF_CUDA_TRY(cudaMemcpyAsync(out, ou, nb, cudaMemcpyDeviceToDevice, st));
   if (drho) WDF_CUDA_TRY(cudaMemcpyAsync(drho, dr, nb, cudaMemcpyDeviceToDevice, st));
@@ -636,10 +726,19 @@ void finish_setup(wdf_ctx *c) {
   // FP32 copy of the projectors and orbitals
   c->U32.ensure(sizeof(cplx<float>) * (size_t)M * g.ld);
   launch_convert<double, float>(g, (float *)c->U32.p, (const double *)c->U64.p, 2 * (size_t)M * g.ld, st);
+  if (c->opt.precision == WDF_MIXED_DF) {  // double-float copies for residuals and density
+    c->Udf.ensure(sizeof(cplx<df64>) * (size_t)M * g.ld);
+    to_df(c, c->Udf.as<cplx<df64>>(), c->U64.as<cplx<double>>(), M);
+    c->vlocdf.ensure(sizeof(df64) * c->ngrid);
+    launch_convert<double, df64>(g, c->vlocdf.as<df64>(), c->vloc64.as<double>(), c->ngrid, st);
+    c->psirdf.ensure(sizeof(df64) * (size_t)nocc * c->ngrid);
+    launch_convert<double, df64>(g, c->psirdf.as<df64>(), c->psir64.as<double>(), (size_t)nocc * c->ngrid, st);
+  }
   WDF_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 template void apply_operator<double>(wdf_ctx *, const cplx<double> *, cplx<double> *, int, const double *, bool);
 template void apply_operator<float>(wdf_ctx *, const cplx<float> *, cplx<float> *, int, const double *, bool);
+template void apply_operator<df64>(wdf_ctx *, const cplx<df64> *, cplx<df64> *, int, const double *, bool);
 
 }  // namespace wdf

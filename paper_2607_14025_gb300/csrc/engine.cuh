@@ -57,10 +57,11 @@ struct wdf_ctx {
   wdf::Geo geo{};
   wdf::FftCtx<double> f64{};
   wdf::FftCtx<float> f32{};
+  wdf::FftCtx<wdf::df64> fdf{};  // double-float instances (WDF_MIXED_DF)
 
   // layout tables
   wdf::DBuf t_col_off, t_col_zlo, t_e_col, t_e_z, t_tile, t_xact, t_pos3, t_g2, t_vhalf;
-  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32, t_xactn, t_jidx;
+  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32, t_twdf, t_xactn, t_jidx;
 
   // operator data
   wdf::DBuf vloc64, vloc32;  // V_loc on the grid
@@ -69,18 +70,20 @@ struct wdf_ctx {
   wdf::DBuf psir64, psir32;  // [nocc][ngrid] psi_v(r) (unnormalised inverse transform)
   wdf::DBuf kp64, kp32;      // [nocc][ld] TPA preconditioner
   wdf::DBuf tkin;            // [nocc]
+  wdf::DBuf vlocdf, Udf, psirdf;  // double-float copies (WDF_MIXED_DF)
   wdf::DBuf eps_dev;         // [nocc]
 
   // workspaces (grow-only)
   struct Cg {
     wdf::DBuf r, z, p, Ap, x, cb, S, part1, part2, dbl, ints;
-  } cg64, cg32;
+  } cg64, cg32, cgdf;
   wdf::DBuf rb, rx, rr, rAx, rwork;        // refinement: b, x, r, A x (FP64), FP32 staging
   wdf::DBuf shift, vidx_dev, thr;          // per-solve shift, orbital index, thresholds
   wdf::DBuf gramw;                         // split partial sums of Gram products
   wdf::DBuf xpert, dvgrid, accgrid, cb2, outi, drhoi, ext_in, ext_out, ext_out2;
   wdf::DBuf dv_V, dv_W, dv_X, dv_AX, dv_R, dv_H, dv_Y, dv_theta, dv_jac, dv_jint, dv_small, dv_neg;
   wdf::DBuf zeros, flag, guess, chi_out, chi_drho;
+  wdf::DBuf dfa, dfb, xpdf, dvgriddf, accgriddf, cb2df, drdf, oudf;  // double-float work
 
   // kernel timing (wdf_profile_kernel)
   wdf::Profiler prof;

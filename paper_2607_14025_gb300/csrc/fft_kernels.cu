@@ -302,6 +302,7 @@ void launch_plane(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, 
   template void launch_plane<T>(const FftCtx<T> &, int, int, const PlaneArgs<T> &, cudaStream_t);
 WDF_INST(double)
 WDF_INST(float)
+WDF_INST(df64)
 #undef WDF_INST
 
 }  // namespace wdf

@@ -184,7 +184,7 @@ void launch_gram(const Geo &g, const cplx<T> *A, int na, const cplx<T> *B, int n
     echunk = ((g.nint + GK - 1) / GK) * GK;
   }
   dim3 grid((na + GI - 1) / GI, (nb + GJ - 1) / GJ, nsplit);
-  typedef typename std::conditional<std::is_same<T, double>::value, double, float>::type Acc;
+  typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type Acc;  // T for FP64 and double-float
   if (nsplit == 1) {
     launch("gram", bits_of<T>(), k_gram<T, Acc>, dim3(grid), dim3(256), 0, st, g, A, na, B, nb, out, ldo, echunk, 0);
   } else {
@@ -315,7 +315,7 @@ void launch_lincomb(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, 
     return;
   }
   dim3 grid((g.nint + LE - 1) / LE, (ny + LS - 1) / LS);
-  typedef typename std::conditional<std::is_same<T, double>::value, double, float>::type Acc;
+  typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type Acc;  // T for FP64 and double-float
   launch("lincomb", bits_of<T>(), k_lincomb<T, Acc>, dim3(grid), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc, d, c0);
   WDF_CUDA_TRY(cudaGetLastError());
 }
@@ -805,5 +805,11 @@ WDF_INST(float)
 #undef WDF_INST
 template void launch_convert<double, float>(const Geo &, float *, const double *, size_t, cudaStream_t);
 template void launch_convert<float, double>(const Geo &, double *, const float *, size_t, cudaStream_t);
+template void launch_convert<double, df64>(const Geo &, df64 *, const double *, size_t, cudaStream_t);
+template void launch_convert<df64, double>(const Geo &, double *, const df64 *, size_t, cudaStream_t);
+template void launch_gram<df64>(const Geo &, const cplx<df64> *, int, const cplx<df64> *, int, double *, int, double *, size_t,
+                                cudaStream_t);
+template void launch_lincomb<df64>(const Geo &, cplx<df64> *, int, const cplx<df64> *, int, const double *, int, const double *,
+                                   double, cudaStream_t);
 
 }  // namespace wdf

@@ -457,7 +457,9 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
 
 template void set_plane_fast_limits<double>(const Geo &);
 template void set_plane_fast_limits<float>(const Geo &);
+template void set_plane_fast_limits<df64>(const Geo &);
 template bool launch_plane_fast<double>(const FftCtx<double> &, int, int, const PlaneArgs<double> &, cudaStream_t);
 template bool launch_plane_fast<float>(const FftCtx<float> &, int, int, const PlaneArgs<float> &, cudaStream_t);
+template bool launch_plane_fast<df64>(const FftCtx<df64> &, int, int, const PlaneArgs<df64> &, cudaStream_t);
 
 }  // namespace wdf

@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "wdf.h")
 
 WDF_OK, WDF_EINVAL, WDF_ENOMEM, WDF_ECUDA, WDF_ENOCONV, WDF_ETIMEOUT, WDF_ENAN, WDF_ESTATE = range(8)
 WDF_MEM_HOST, WDF_MEM_DEVICE = 0, 1
-WDF_FP64, WDF_MIXED = 0, 1
+WDF_FP64, WDF_MIXED, WDF_MIXED_DF = 0, 1, 2
 WDF_PRECOND_NONE, WDF_PRECOND_TPA = 0, 1
 
 
@@ -182,7 +182,7 @@ class Context:
         self._ctx = ctypes.c_void_p()
         opt = _Options()
         self._lib.wdf_default_options(ctypes.byref(opt))
-        opt.precision = {"fp64": WDF_FP64, "mixed": WDF_MIXED}[precision]
+        opt.precision = {"fp64": WDF_FP64, "mixed": WDF_MIXED, "mixed_df": WDF_MIXED_DF}[precision]
         opt.precond = {"none": WDF_PRECOND_NONE, "tpa": WDF_PRECOND_TPA}[precond]
         opt.cg_tol, opt.cg_maxiter, opt.inner_tol, opt.alpha = cg_tol, cg_maxiter, inner_tol, alpha
         opt.max_batch, opt.gs_tol, opt.gs_maxiter, opt.gs_extra = max_batch, gs_tol, gs_maxiter, gs_extra

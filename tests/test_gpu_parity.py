@@ -84,16 +84,29 @@ def test_chi0_fp64_matches_oracle(name, npert):
     assert rel(out, ref["out"]) < 1e-8
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
 @pytest.mark.parametrize("name", ["tiny", "ragged"])
-def test_chi0_mixed_matches_oracle(name):
+def test_chi0_mixed_matches_oracle(name, prec):
     s, H, w, psi, R = oracle_state(name)
     phi = synth.make_perturbations(s, 4, 12)
     ref = R.apply(phi, tol=1e-13)
-    with wdf.Context(s, precision="mixed", cg_tol=1e-10, gs_tol=1e-11) as c:
+    with wdf.Context(s, precision=prec, cg_tol=1e-10, gs_tol=1e-11) as c:
         out, drho, st = c.apply_chi0(phi, want_drho=True)
     assert st.max_residual <= 1e-10
     assert rel(drho, ref["drho"]) < 1e-8
     assert rel(out, ref["out"]) < 1e-8
+
+
+def test_chi0_double_float_resolves_tight_residuals():
+    # double-float residuals, right-hand sides and density (about 48 bits) certify 1e-12
+    s, H, w, psi, R = oracle_state("small")
+    phi = synth.make_perturbations(s, 5, 14)
+    ref = R.apply(phi, tol=1e-13)
+    with wdf.Context(s, precision="mixed_df", cg_tol=1e-12, gs_tol=1e-11) as c:
+        out, drho, st = c.apply_chi0(phi, want_drho=True)
+    assert st.max_residual <= 1e-12
+    assert rel(drho, ref["drho"]) < 1e-10
+    assert rel(out, ref["out"]) < 1e-10
 
 
 def test_chi0_default_tolerance_error_report():
@@ -102,7 +115,7 @@ def test_chi0_default_tolerance_error_report():
     s, H, w, psi, R = oracle_state("small")
     phi = synth.make_perturbations(s, 4, 13)
     ref = R.apply(phi, tol=1e-13)
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_df"):
         with wdf.Context(s, precision=prec, cg_tol=1e-8, gs_tol=1e-11) as c:
             out, drho, st = c.apply_chi0(phi, want_drho=True)
         assert st.max_residual <= 1e-8
