@@ -13,6 +13,8 @@
 //    pointwise product (V_loc, or psi_v times dV) and the orbital sum of the density response
 //    stay in registers.
 //  * All index arithmetic is on compile-time sizes.
+#include <cstdlib>
+
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -391,6 +393,160 @@ __global__ void __launch_bounds__(PlaneShape<N>::threads) k_plane_fast(Geo g, co
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32 V_loc plane kernel with whole lines in registers (n1 = n2 = N = 8 R2, R2 in {3, 4, 5, 8}).
+// One thread owns one line of N complex values: a four-step DFT with static register indices
+// (8-point DFTs over stride-R2 subsequences, twiddles, R2-point DFTs over consecutive slots).
+// The inverse takes natural order and leaves X[k1 + 8 k2] in slot k2 + R2 k1; the forward
+// transform takes exactly that permuted order and returns natural order, so the n1 inverse, the
+// V_loc product and the n1 forward transform of a row never leave registers. Shared memory only
+// carries the two transpositions between columns (n2 transforms) and rows (n1 transforms).
+
+template <int N>
+__device__ __forceinline__ void line_inverse(float2 (&x)[N], const float2 *tw) {
+  constexpr int R2 = N / 8;
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    float2 a[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) a[n1] = x[n2 + R2 * n1];
+    dft_reg<float, 8>(a, 1.f);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) x[n2 + R2 * k1] = (n2 * k1 == 0) ? a[k1] : cmul<float>(a[k1], tw[n2 * k1]);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    float2 b[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) b[n2] = x[n2 + R2 * k1];
+    dft_reg<float, R2>(b, 1.f);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k2 + R2 * k1] = b[k2];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void line_forward(float2 (&x)[N], const float2 *tw) {
+  constexpr int R2 = N / 8;
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    float2 b[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) b[k2] = x[k2 + R2 * k1];
+    dft_reg<float, R2>(b, -1.f);
+#pragma unroll
+    for (int q2 = 0; q2 < R2; ++q2) x[q2 + R2 * k1] = (k1 * q2 == 0) ? b[q2] : cmulc<float>(b[q2], tw[k1 * q2]);
+  }
+#pragma unroll
+  for (int q2 = 0; q2 < R2; ++q2) {
+    float2 a[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) a[k1] = x[q2 + R2 * k1];
+    dft_reg<float, 8>(a, -1.f);
+#pragma unroll
+    for (int q1 = 0; q1 < 8; ++q1) x[q2 + R2 * q1] = a[q1];
+  }
+}
+
+// natural index held by slot s after line_inverse
+template <int N> __device__ __forceinline__ constexpr int perm_index(int s) { return s / (N / 8) + 8 * (s % (N / 8)); }
+
+template <int N>
+__global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jidx,
+                                                 PlaneArgs<float> pa) {
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 *tw = reinterpret_cast<float2 *>(smraw);
+  float2 *tile = tw + N;
+  float *vsm = reinterpret_cast<float *>(tile + N * P);
+  int *xact = reinterpret_cast<int *>(vsm + N * P);
+  const int t = threadIdx.x, z = blockIdx.y, q = blockIdx.x;
+  const int nx = g.nxact, xmax = g.xmax;
+  tw[t] = twg[t];
+  for (int i = t; i < nx; i += N) xact[i] = g.xactn[i];
+  const float *vz = pa.field + (size_t)z * N * N;
+  for (int i = t; i < N * N; i += N) vsm[(i / N) * P + (i % N)] = vz[i];  // coalesced, padded rows
+  __syncthreads();
+  float2 *cbz = pa.cb + (size_t)q * g.n3 * g.ldcb + (size_t)z * g.ldcb;
+  float2 v[N];
+  if (t < nx) {  // inverse along n2 of occupied column x
+    const int x = xact[t];
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int jj = __ldg(jidx + y * N + x);
+      v[y] = jj >= 0 ? cbz[jj] : mkc<float>(0.f, 0.f);
+    }
+    line_inverse<N>(v, tw);
+#pragma unroll
+    for (int s = 0; s < N; ++s) tile[perm_index<N>(s) * P + x] = v[s];
+  }
+  __syncthreads();
+  {  // row y = t: inverse along n1, V_loc, forward along n1 (each thread touches its own row only)
+    const int y = t;
+#pragma unroll
+    for (int x = 0; x < N; ++x) v[x] = (x <= xmax || x >= N - xmax) ? tile[y * P + x] : mkc<float>(0.f, 0.f);
+    line_inverse<N>(v, tw);
+#pragma unroll
+    for (int s = 0; s < N; ++s) v[s] = cscal<float>(v[s], vsm[y * P + perm_index<N>(s)]);
+    line_forward<N>(v, tw);
+#pragma unroll
+    for (int x = 0; x < N; ++x)
+      if (x <= xmax || x >= N - xmax) tile[y * P + x] = v[x];
+  }
+  __syncthreads();
+  if (t < nx) {  // forward along n2 of occupied column x, scattered back to the column buffer
+    const int x = xact[t];
+#pragma unroll
+    for (int s = 0; s < N; ++s) v[s] = tile[perm_index<N>(s) * P + x];
+    line_forward<N>(v, tw);
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int jj = __ldg(jidx + y * N + x);
+      if (jj >= 0) cbz[jj] = v[y];
+    }
+  }
+}
+
+template <int N> size_t reg_smem(const Geo &g) {
+  return sizeof(float2) * ((size_t)N + (size_t)N * (N + 1)) + sizeof(float) * (size_t)N * (N + 1) + sizeof(int) * (size_t)g.nxact;
+}
+
+template <int N> static void launch_reg(const FftCtx<float> &f, int nblk, const PlaneArgs<float> &pa, cudaStream_t st) {
+  launch("plane_vloc", 32, k_plane_reg<N>, dim3(nblk, f.g.n3), dim3(N), reg_smem<N>(f.g), st, f.g, f.tw1, f.jidx, pa);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+// sizes with the register kernel: N = 8 R2, R2 in {3, 4, 5, 8}
+#define WDF_REG_SIZES(X) X(24) X(32) X(40) X(64)
+
+static bool reg_plane_enabled() {
+  static const bool on = std::getenv("WDF_NO_REG_PLANE") == nullptr;
+  return on;
+}
+
+void set_plane_reg_limits(const Geo &g) {
+  switch (g.n1) {
+#define X(N)                                                                                                   \
+  case N:                                                                                                      \
+    WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane_reg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reg_smem<N>(g))); \
+    break;
+    WDF_REG_SIZES(X)
+#undef X
+    default: break;
+  }
+}
+
+static bool launch_plane_reg(const FftCtx<float> &f, int nblk, const PlaneArgs<float> &pa, cudaStream_t st) {
+  if (!reg_plane_enabled() || f.g.n1 != f.g.n2) return false;
+  switch (f.g.n1) {
+#define X(N) \
+  case N: launch_reg<N>(f, nblk, pa, st); return true;
+    WDF_REG_SIZES(X)
+#undef X
+    default: return false;
+  }
+}
+
 template <typename T, int N> size_t fast_smem(const Geo &g) {
   return sizeof(cplx<T>) * ((size_t)N + (size_t)N * (N + 1)) + sizeof(int) * (size_t)g.nxact;
 }
@@ -433,6 +589,7 @@ bool plane_fast_supported(int n1, int n2) {
 }
 
 template <typename T> void set_plane_fast_limits(const Geo &g) {
+  if (std::is_same<T, float>::value && g.n1 == g.n2) set_plane_reg_limits(g);
   switch (g.n1) {
 #define X(N) \
   case N: set_limits<T, N>(g); break;
@@ -445,7 +602,11 @@ template <typename T> void set_plane_fast_limits(const Geo &g) {
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st) {
   // the orbital sum of the density response keeps two register blocks across its loop and
   // spills here; it runs once per chi0 application and stays on the generic kernel
-  if (op == OP_ACCUM || f.jidx == nullptr || !plane_fast_supported(f.g.n1, f.g.n2)) return false;
+  if (op == OP_ACCUM || f.jidx == nullptr) return false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (op == OP_VLOC && launch_plane_reg(f, nblk, pa, st)) return true;
+  }
+  if (!plane_fast_supported(f.g.n1, f.g.n2)) return false;
   switch (f.g.n1) {
 #define X(N) \
   case N: launch_n<T, N>(f, op, nblk, pa, st); return true;
