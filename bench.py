@@ -114,6 +114,27 @@ def oracle_sample(system_name: str, nsolve_target: int = 64):
     return s, R, phi, t_gs
 
 
+def rank_block_seed(rank: int) -> int:
+    """Seed of the perturbation block a rank owns (blocks are independent: no exchange)."""
+    return 1000 + rank
+
+
+def reduce_step_times(times, device=None):
+    """Max over ranks of each per-step time (the slowest rank sets the job's pace)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_throughput(world: int, units_per_rank: int, ms_max: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -172,7 +193,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     s = synth.make_system(WORKLOAD)
     # each rank applies chi0bar to its own seeded perturbation block (weak scaling)
-    phi_h = synth.make_perturbations(s, NPERT, 1000 + rank)
+    phi_h = synth.make_perturbations(s, NPERT, rank_block_seed(rank))
     t_setup = time.perf_counter()
     ctx = wdf.Context(s, precision=args.precision, cg_tol=1e-8, stream=stream.cuda_stream, device=local,
                       max_batch=args.max_batch)
@@ -235,14 +256,11 @@ def run_gpu(args):
             lam_h, vec_h, st_h = step(phi_h)
         torch.cuda.synchronize(dev)
         ms_e2e = 1e3 * (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_dev, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_dev, ms_e2e = float(t[0]), float(t[1])
+    ms_dev, ms_e2e = reduce_step_times([ms_dev, ms_e2e], device=dev)
     nsolve = stats[-1]["nsolve"]
     iters = stats[-1]["cg_iters"] / max(1, nsolve)
-    value = world * nsolve / (ms_dev * 1e-3)
-    e2e = world * nsolve / (ms_e2e * 1e-3)
+    value = job_throughput(world, nsolve, ms_dev)
+    e2e = job_throughput(world, nsolve, ms_e2e)
     ctx.close()
     if rank != 0:
         return
@@ -264,7 +282,7 @@ def run_gpu(args):
                                "64 occupied, 128 perturbations per GPU, PDEP 64 eigenpairs, one Davidson iteration per step",
                    "precision": args.precision, "cg_tol": 1e-8, "l2": "flushed (256 MiB write) before each step; working set > L2",
                    "parallelism": f"perturbation blocks x{world}"},
-        "chi0_applies_per_s": world * NPERT / (ms_dev * 1e-3),
+        "chi0_applies_per_s": job_throughput(world, NPERT, ms_dev),
         "cg_iters_per_solve": iters,
         "max_residual": stats[-1]["max_residual"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,

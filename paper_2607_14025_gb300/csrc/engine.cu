@@ -169,6 +169,39 @@ void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const doubl
   }
 }
 
+// The CG's operator application: like apply_operator with the shift and the occupied-space term,
+// plus (dir != null) the direction update p = K r + beta p folded into the first transform, and
+// the partial sums of <p, A p> from the epilogue of the last linear combination. Returns the
+// number of partial sums per solve written to dotpart, or 0 if they were not computed.
+template <typename T>
+static int apply_operator_cg(wdf_ctx *c, cplx<T> *X, cplx<T> *Y, int n, const double *shift, const PDir<T> *dir, double *dotpart) {
+  const FftCtx<T> &f = Prec<T>::f(c);
+  const Geo &g = c->geo;
+  wdf_ctx::Cg &w = Prec<T>::cg(c);
+  const int npair = (n + 1) / 2;
+  w.cb.ensure(sizeof(cplx<T>) * (size_t)npair * g.n3 * g.ldcb);
+  cplx<T> *cb = w.cb.as<cplx<T>>();
+  if (dir) launch_zpass_g2r_dir<T>(f, *dir, n, cb, c->st);
+  else launch_zpass_g2r<T>(f, X, n, cb, c->st);
+  PlaneArgs<T> pa;
+  pa.cb = cb;
+  pa.field = Prec<T>::vloc(c);
+  launch_plane<T>(f, OP_VLOC, npair, pa, c->st);
+  EpiArgs<T> ea;
+  ea.Y = Y;
+  ea.X = X;
+  ea.shift = shift;
+  ea.scale = (T)(1.0 / (double)c->ngrid);
+  launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, n, ea, c->st);
+  const int M = c->nproj + c->nocc;
+  w.S.ensure(sizeof(double) * (size_t)M * n);
+  gram<T>(c, Prec<T>::U(c), M, X, n, w.S.as<double>(), n);
+  if (launch_lincomb_dot<T>(g, Y, n, Prec<T>::U(c), M, w.S.as<double>(), n, c->lrd.as<double>(), 1.0, X, dotpart, c->st))
+    return lincomb_dot_chunks(g);
+  launch_lincomb<T>(g, Y, n, Prec<T>::U(c), M, w.S.as<double>(), n, c->lrd.as<double>(), 1.0, c->st);
+  return 0;
+}
+
 // ---------------------------------------------------------------------------------------------
 // preconditioned conjugate gradients on (H - eps_v + alpha P) d = b, one solve per row
 
@@ -182,7 +215,7 @@ static void cg_solve(wdf_ctx *c, const cplx<T> *b, cplx<T> *x, int n, int maxite
   w.p.ensure(vb);
   w.Ap.ensure(vb);
   const int nch = dot_chunks(g);
-  w.part1.ensure(sizeof(double) * (size_t)n * nch);
+  w.part1.ensure(sizeof(double) * (size_t)n * std::max(nch, lincomb_dot_chunks(g)));
   w.part2.ensure(sizeof(double) * (size_t)n * nch);
   w.dbl.ensure(sizeof(double) * 4 * (size_t)n);
   w.ints.ensure(sizeof(int) * (2 * (size_t)n + 1));
@@ -208,19 +241,30 @@ static void cg_solve(wdf_ctx *c, const cplx<T> *b, cplx<T> *x, int n, int maxite
   WDF_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
   WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
   WDF_CUDA_TRY(cudaMemsetAsync(ii, 0, sizeof(int) * (2 * (size_t)n + 1), st));
-  launch_cg_start<T>(g, r, z, p, K, s, n, nch, st);
+  (void)z;  // z = K r is not stored: the update and the direction recompute it
+  launch_cg_start<T>(g, r, nullptr, p, K, s, n, nch, st);
   launch_cg_scalars(s, n, nch, 2, maxiter, st);
   int nact = 0;
   WDF_CUDA_TRY(cudaMemcpyAsync(&nact, s.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
   WDF_CUDA_TRY(cudaStreamSynchronize(st));
+  PDir<T> dir;
+  dir.p = p;
+  dir.r = r;
+  dir.K = K;
+  dir.vidx = s.vidx;
+  dir.active = s.active;
+  dir.beta = s.rz_new;
   for (int it = 0; it < maxiter && nact > 0; ++it) {
-    apply_operator<T>(c, p, Ap, n, s.shift, true);
-    launch_dot_partial<T>(g, p, Ap, n, s.part1, nch, st);
-    launch_cg_scalars(s, n, nch, 0, maxiter, st);
-    launch_cg_update<T>(g, x, r, z, p, Ap, K, s, n, nch, st);
+    // p = K r + beta p (from the second iteration on), A p and the partial sums of <p, A p>
+    int ndot = apply_operator_cg<T>(c, p, Ap, n, s.shift, it > 0 ? &dir : nullptr, s.part1);
+    if (ndot == 0) {
+      launch_dot_partial<T>(g, p, Ap, n, s.part1, nch, st);
+      ndot = nch;
+    }
+    launch_cg_scalars(s, n, ndot, 0, maxiter, st);
+    launch_cg_update<T>(g, x, r, nullptr, p, Ap, K, s, n, nch, st);
     WDF_CUDA_TRY(cudaMemsetAsync(s.nactive, 0, sizeof(int), st));
     launch_cg_scalars(s, n, nch, 1, maxiter, st);
-    launch_cg_direction<T>(g, p, z, s, n, st);
     WDF_CUDA_TRY(cudaMemcpyAsync(&nact, s.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     WDF_CUDA_TRY(cudaStreamSynchronize(st));
   }

@@ -28,9 +28,9 @@ static __device__ __forceinline__ int wrap(int z, int n) {
 // ---------------------------------------------------------------------------------------------
 // n3 transforms, G -> r
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_zpass_g2r(const cplx<T> *__restrict__ X, int nvec, Geo g, Plan1D P3,
-                                                         const cplx<T> *__restrict__ tw3, cplx<T> *__restrict__ cb) {
+template <typename T, bool DIR>
+__global__ void __launch_bounds__(kThreads) k_zpass_g2r(const cplx<T> *X, int nvec, Geo g, Plan1D P3,
+                                                         const cplx<T> *__restrict__ tw3, cplx<T> *__restrict__ cb, PDir<T> pd) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T> *tw = reinterpret_cast<cplx<T> *>(smraw);
   cplx<T> *sm = tw + kMaxN;
@@ -44,10 +44,29 @@ __global__ void __launch_bounds__(kThreads) k_zpass_g2r(const cplx<T> *__restric
   const int e0 = g.col_off[k0], e1 = g.col_off[kend];
   const cplx<T> *xa = X + (size_t)(2 * q) * g.ld;
   const cplx<T> *xb = (2 * q + 1 < nvec) ? X + (size_t)(2 * q + 1) * g.ld : nullptr;
+  const int sa = 2 * q, sb = 2 * q + 1;
+  const bool upa = DIR && pd.active[sa], upb = DIR && xb && pd.active[sb];
+  const T *Ka = (DIR && pd.K) ? pd.K + (size_t)pd.vidx[sa] * g.ld : nullptr;
+  const T *Kb = (DIR && pd.K && xb) ? pd.K + (size_t)pd.vidx[sb] * g.ld : nullptr;
+  const T ba = DIR ? (T)pd.beta[sa] : (T)0, bbeta = (DIR && xb) ? (T)pd.beta[sb] : (T)0;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int k = g.e_col[e], c = k - k0, z = g.e_z[e];
-    const cplx<T> a = xa[e];
-    const cplx<T> b = xb ? xb[e] : mkc<T>(0, 0);
+    cplx<T> a = xa[e];
+    cplx<T> b = xb ? xb[e] : mkc<T>(0, 0);
+    if (DIR) {  // p = K r + beta p, written back (each element belongs to exactly one block)
+      if (upa) {
+        const cplx<T> rv = pd.r[(size_t)sa * g.ld + e];
+        const T kk = Ka ? Ka[e] : (T)1;
+        a = mkc<T>(kk * rv.x + ba * a.x, kk * rv.y + ba * a.y);
+        pd.p[(size_t)sa * g.ld + e] = a;
+      }
+      if (upb) {
+        const cplx<T> rv = pd.r[(size_t)sb * g.ld + e];
+        const T kk = Kb ? Kb[e] : (T)1;
+        b = mkc<T>(kk * rv.x + bbeta * b.x, kk * rv.y + bbeta * b.y);
+        pd.p[(size_t)sb * g.ld + e] = b;
+      }
+    }
     sm[c * pitch + g.pos3[wrap(z, n3)]] = mkc<T>(a.x - b.y, a.y + b.x);  // a + i b at G
     if (k != 0) sm[(kZCols + c) * pitch + g.pos3[wrap(-z, n3)]] = mkc<T>(a.x + b.y, b.x - a.y);  // at -G
   }
@@ -247,7 +266,8 @@ template <typename T> size_t plane_smem(const Geo &g) {
 template <typename T>
 void set_fft_smem_limits(const Geo &g) {
   const int zs = (int)zpass_smem<T>(g), ps = (int)plane_smem<T>(g);
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_g2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
+  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_g2r<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
+  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_g2r<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
   WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_r2g<T, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
   WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_r2g<T, EPI_HSHIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
   WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_r2g<T, EPI_DRHO>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
@@ -262,7 +282,17 @@ template <typename T>
 void launch_zpass_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st) {
   if (nvec <= 0) return;
   dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
-  launch("zpass_g2r", bits_of<T>(), k_zpass_g2r<T>, dim3(grid), dim3(kThreads), zpass_smem<T>(f.g), st, X, nvec, f.g, f.P3, f.tw3, cb);
+  launch("zpass_g2r", bits_of<T>(), k_zpass_g2r<T, false>, dim3(grid), dim3(kThreads), zpass_smem<T>(f.g), st, X, nvec, f.g, f.P3,
+         f.tw3, cb, PDir<T>());
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+template <typename T>
+void launch_zpass_g2r_dir(const FftCtx<T> &f, const PDir<T> &d, int nvec, cplx<T> *cb, cudaStream_t st) {
+  if (nvec <= 0) return;
+  dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
+  launch("zpass_g2r", bits_of<T>(), k_zpass_g2r<T, true>, dim3(grid), dim3(kThreads), zpass_smem<T>(f.g), st,
+         (const cplx<T> *)d.p, nvec, f.g, f.P3, f.tw3, cb, d);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -297,6 +327,7 @@ void launch_plane(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, 
   template size_t plane_smem<T>(const Geo &);                                                               \
   template size_t zpass_smem<T>(const Geo &);                                                               \
   template void launch_zpass_g2r<T>(const FftCtx<T> &, const cplx<T> *, int, cplx<T> *, cudaStream_t);      \
+  template void launch_zpass_g2r_dir<T>(const FftCtx<T> &, const PDir<T> &, int, cplx<T> *, cudaStream_t);  \
   template void launch_zpass_r2g<T>(const FftCtx<T> &, int, const cplx<T> *, int, const EpiArgs<T> &,       \
                                     cudaStream_t);                                                          \
   template void launch_plane<T>(const FftCtx<T> &, int, int, const PlaneArgs<T> &, cudaStream_t);

@@ -42,7 +42,17 @@ template <typename T> void set_plane_fast_limits(const Geo &g);
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
 template <typename T> size_t plane_smem(const Geo &g);
 template <typename T> size_t zpass_smem(const Geo &g);
+// CG direction update folded into the first transform: p = K r + beta p for active solves
+template <typename T> struct PDir {
+  cplx<T> *p = nullptr;          // also the transformed vectors
+  const cplx<T> *r = nullptr;
+  const T *K = nullptr;          // [nocc][ld] preconditioner, or null (identity)
+  const int *vidx = nullptr, *active = nullptr;
+  const double *beta = nullptr;
+};
 template <typename T> void launch_zpass_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st);
+template <typename T>
+void launch_zpass_g2r_dir(const FftCtx<T> &f, const PDir<T> &d, int nvec, cplx<T> *cb, cudaStream_t st);
 template <typename T>
 void launch_zpass_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st);
 template <typename T> void launch_plane(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
@@ -60,6 +70,12 @@ size_t gram_work_doubles(const Geo &g, int na, int nb, int ldo);
 template <typename T>
 void launch_lincomb(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, const double *C, int ldc,
                     const double *d, double c0, cudaStream_t st);
+// launch_lincomb plus partial inner products <P_s, Y_s> of the results, written to
+// part[s * lincomb_dot_chunks(g) + block]; returns false (nothing launched) for ny <= 8
+template <typename T>
+bool launch_lincomb_dot(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, const double *C, int ldc, const double *d,
+                        double c0, const cplx<T> *P, double *part, cudaStream_t st);
+int lincomb_dot_chunks(const Geo &g);
 // per-vector partial inner products: part[s * nchunk + c] over element chunk c
 template <typename T>
 void launch_dot_partial(const Geo &g, const cplx<T> *A, const cplx<T> *B, int nvec, double *part, int nchunk,

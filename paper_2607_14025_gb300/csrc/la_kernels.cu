@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const cplx<T> *__restrict__
 #pragma unroll
       for (int a = 0; a < 4; ++a) av[a] = As[k][ty * 4 + a];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) bv[b] = Bs[k][tx * 8 + b];
+      for (int b = 0; b < 8; ++b) bv[b] = Bs[k][tx + 16 * b];  // consecutive lanes: consecutive banks
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -98,7 +98,86 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const cplx<T> *__restrict__
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-      const int i = i0 + ty * 4 + a, j = j0 + tx * 8 + b;
+      const int i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
+      if (i < na && j < nb) o[(size_t)i * ldo + j] = (double)acc[a][b];
+    }
+}
+
+// FP32 Gram products: the same 64 x 128 block tile with 4 x 8 register tiles, 32-element chunks,
+// and the next chunk's global loads issued before the current chunk's arithmetic (register
+// prefetch), so memory latency overlaps the FMAs.
+constexpr int GK32 = 32;
+
+__global__ void __launch_bounds__(256) k_gram_f32(Geo g, const float2 *__restrict__ A, int na, const float2 *__restrict__ B, int nb,
+                                                 double *__restrict__ out, int ldo, int echunk, size_t split_stride) {
+  __shared__ float2 As[GK32][GI];
+  __shared__ float2 Bs[GK32][GJ];
+  const int i0 = blockIdx.x * GI, j0 = blockIdx.y * GJ;
+  const int ebeg = blockIdx.z * echunk;
+  const int eend = min(g.nint, ebeg + echunk);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  constexpr int LA = GI * GK32 / 256, LB = GJ * GK32 / 256;  // elements loaded per thread: 8, 16
+  float2 ra[LA], rb[LB];
+  auto load = [&](int e0) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      const int row = t / GK32, col = t % GK32, e = e0 + col;
+      float2 a = make_float2(0.f, 0.f);
+      if (e < eend && i0 + row < na) {
+        a = A[(size_t)(i0 + row) * g.ld + e];
+        const float w = e < g.len0 ? 1.f : 2.f;
+        a.x *= w;
+        a.y *= w;
+      }
+      ra[u] = a;
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      const int row = t / GK32, col = t % GK32, e = e0 + col;
+      rb[u] = (e < eend && j0 + row < nb) ? B[(size_t)(j0 + row) * g.ld + e] : make_float2(0.f, 0.f);
+    }
+  };
+  float acc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  if (ebeg < eend) load(ebeg);
+  for (int e0 = ebeg; e0 < eend; e0 += GK32) {
+    __syncthreads();  // the previous chunk's arithmetic is done with the tiles
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      As[t % GK32][t / GK32] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      Bs[t % GK32][t / GK32] = rb[u];
+    }
+    __syncthreads();
+    if (e0 + GK32 < eend) load(e0 + GK32);
+#pragma unroll 8
+    for (int k = 0; k < GK32; ++k) {
+      float2 av[4], bv[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[k][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) bv[b] = Bs[k][tx + 16 * b];  // consecutive lanes: consecutive banks
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a].x, bv[b].x, fmaf(av[a].y, bv[b].y, acc[a][b]));
+    }
+  }
+  double *o = out + blockIdx.z * split_stride;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
       if (i < na && j < nb) o[(size_t)i * ldo + j] = (double)acc[a][b];
     }
 }
@@ -185,6 +264,19 @@ void launch_gram(const Geo &g, const cplx<T> *A, int na, const cplx<T> *B, int n
   }
   dim3 grid((na + GI - 1) / GI, (nb + GJ - 1) / GJ, nsplit);
   typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type Acc;  // T for FP64 and double-float
+  if constexpr (std::is_same<T, float>::value) {
+    echunk = ((echunk + GK32 - 1) / GK32) * GK32;  // whole 32-element chunks per split
+    grid.z = nsplit = (g.nint + echunk - 1) / echunk;
+    if (nsplit == 1) {
+      launch("gram", 32, k_gram_f32, dim3(grid), dim3(256), 0, st, g, A, na, B, nb, out, ldo, echunk, (size_t)0);
+    } else {
+      launch("gram", 32, k_gram_f32, dim3(grid), dim3(256), 0, st, g, A, na, B, nb, work, ldo, echunk, stride);
+      WDF_CUDA_TRY(cudaGetLastError());
+      launch("gram_sum", 0, k_sum_splits, dim3((na * nb + 255) / 256), dim3(256), 0, st, work, nsplit, stride, out, na, nb, ldo);
+    }
+    WDF_CUDA_TRY(cudaGetLastError());
+    return;
+  }
   if (nsplit == 1) {
     launch("gram", bits_of<T>(), k_gram<T, Acc>, dim3(grid), dim3(256), 0, st, g, A, na, B, nb, out, ldo, echunk, 0);
   } else {
@@ -208,7 +300,8 @@ template <typename T> __host__ __device__ constexpr int lj_rows() { return sizeo
 
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y, int ny, const cplx<T> *__restrict__ U, int nu,
-                                                const double *__restrict__ C, int ldc, const double *__restrict__ d, double c0) {
+                                                const double *__restrict__ C, int ldc, const double *__restrict__ d, double c0,
+                                                const cplx<T> *__restrict__ P, double *__restrict__ part) {
   constexpr int LJ = lj_rows<T>();
   __shared__ Acc cs[LJ][LS];
   __shared__ cplx<T> us[LJ][LE];
@@ -251,6 +344,7 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
     }
     __syncthreads();
   }
+  double dsum[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int s = s0 + ts * 4 + q;
@@ -260,12 +354,27 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
       const int e = e0 + te + 32 * p;
       if (e >= g.nint) continue;
       cplx<T> *y = Y + (size_t)s * g.ld + e;
+      cplx<T> yv;
       if (c0 == 0.0) {
-        *y = mkc<T>((T)ax[p][q], (T)ay[p][q]);
+        yv = mkc<T>((T)ax[p][q], (T)ay[p][q]);
       } else {
         const cplx<T> o = *y;
-        *y = mkc<T>((T)((Acc)c0 * (Acc)o.x + ax[p][q]), (T)((Acc)c0 * (Acc)o.y + ay[p][q]));
+        yv = mkc<T>((T)((Acc)c0 * (Acc)o.x + ax[p][q]), (T)((Acc)c0 * (Acc)o.y + ay[p][q]));
       }
+      *y = yv;
+      if (part) {  // partial inner products <P_s, Y_s> over this block's elements
+        const cplx<T> pv = P[(size_t)s * g.ld + e];
+        dsum[q] += wgt(e, g.len0) * ((double)pv.x * (double)yv.x + (double)pv.y * (double)yv.y);
+      }
+    }
+  }
+  if (part) {  // a warp holds vectors 4 ts .. 4 ts + 3 across its 32 lanes: reduce over lanes
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double v = dsum[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      const int s = s0 + ts * 4 + q;
+      if (te == 0 && s < ny) part[(size_t)s * gridDim.x + blockIdx.x] = v;
     }
   }
 }
@@ -316,8 +425,22 @@ void launch_lincomb(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, 
   }
   dim3 grid((g.nint + LE - 1) / LE, (ny + LS - 1) / LS);
   typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type Acc;  // T for FP64 and double-float
-  launch("lincomb", bits_of<T>(), k_lincomb<T, Acc>, dim3(grid), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc, d, c0);
+  launch("lincomb", bits_of<T>(), k_lincomb<T, Acc>, dim3(grid), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc, d, c0,
+         (const cplx<T> *)nullptr, (double *)nullptr);
   WDF_CUDA_TRY(cudaGetLastError());
+}
+
+int lincomb_dot_chunks(const Geo &g) { return (g.nint + LE - 1) / LE; }
+
+template <typename T>
+bool launch_lincomb_dot(const Geo &g, cplx<T> *Y, int ny, const cplx<T> *U, int nu, const double *C, int ldc, const double *d,
+                        double c0, const cplx<T> *P, double *part, cudaStream_t st) {
+  if (ny <= kNarrow) return false;  // the narrow kernel has no dot epilogue
+  dim3 grid((g.nint + LE - 1) / LE, (ny + LS - 1) / LS);
+  typedef typename std::conditional<std::is_same<T, float>::value, float, T>::type Acc;
+  launch("lincomb", bits_of<T>(), k_lincomb<T, Acc>, dim3(grid), dim3(256), 0, st, g, Y, ny, U, nu, C, ldc, d, c0, P, part);
+  WDF_CUDA_TRY(cudaGetLastError());
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -349,7 +472,7 @@ void launch_dot_partial(const Geo &g, const cplx<T> *A, const cplx<T> *B, int nv
 // conjugate gradients
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_start(Geo g, const cplx<T> *__restrict__ r, cplx<T> *__restrict__ z,
+__global__ void __launch_bounds__(256) k_cg_start(Geo g, const cplx<T> *__restrict__ r, cplx<T> *z,
                                                  cplx<T> *__restrict__ p, const T *__restrict__ kprec, CgState s, int nchunk) {
   const int i = blockIdx.x, c = blockIdx.y;
   const int e0 = c * DCHUNK, e1 = min(g.nint, e0 + DCHUNK);
@@ -360,7 +483,7 @@ __global__ void __launch_bounds__(256) k_cg_start(Geo g, const cplx<T> *__restri
     const cplx<T> rv = r[o + e];
     const T k = K ? K[e] : (T)1;
     const cplx<T> zv = mkc<T>(k * rv.x, k * rv.y);
-    z[o + e] = zv;
+    if (z) z[o + e] = zv;
     p[o + e] = zv;
     const double w = wgt(e, g.len0);
     vrz += w * dre<T>(rv, zv);
@@ -383,7 +506,7 @@ void launch_cg_start(const Geo &g, const cplx<T> *r, cplx<T> *z, cplx<T> *p, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_update(Geo g, cplx<T> *__restrict__ x, cplx<T> *__restrict__ r, cplx<T> *__restrict__ z,
+__global__ void __launch_bounds__(256) k_cg_update(Geo g, cplx<T> *__restrict__ x, cplx<T> *__restrict__ r, cplx<T> *z,
                                                   const cplx<T> *__restrict__ p, const cplx<T> *__restrict__ Ap,
                                                   const T *__restrict__ kprec, CgState s, int nchunk) {
   const int i = blockIdx.x, c = blockIdx.y;
@@ -404,7 +527,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo g, cplx<T> *__restrict__ 
       r[o + e] = rv;
       const T k = K ? K[e] : (T)1;
       const cplx<T> zv = mkc<T>(k * rv.x, k * rv.y);
-      z[o + e] = zv;
+      if (z) z[o + e] = zv;  // z = K r is recomputed where needed when not stored
       const double w = wgt(e, g.len0);
       vrz += w * dre<T>(rv, zv);
       vrr += w * dre<T>(rv, rv);
@@ -450,10 +573,9 @@ __global__ void k_cg_scalars(CgState s, int n, int nchunk, int which, int maxite
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double a = 0.0, b = 0.0;
-  for (int c = 0; c < nchunk; ++c) {
-    a += s.part1[(size_t)i * nchunk + c];
-    b += s.part2[(size_t)i * nchunk + c];
-  }
+  for (int c = 0; c < nchunk; ++c) a += s.part1[(size_t)i * nchunk + c];
+  if (which != 0)
+    for (int c = 0; c < nchunk; ++c) b += s.part2[(size_t)i * nchunk + c];
   if (which == 0) {
     s.pap[i] = a;
     if (s.active[i] && !(a > 0.0)) s.active[i] = 0;  // breakdown: keep the current iterate
@@ -795,6 +917,8 @@ void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int 
   template void launch_cg_update<T>(const Geo &, cplx<T> *, cplx<T> *, cplx<T> *, const cplx<T> *, const cplx<T> *,     \
                                     const T *, const CgState &, int, int, cudaStream_t);                             \
   template void launch_cg_direction<T>(const Geo &, cplx<T> *, const cplx<T> *, const CgState &, int, cudaStream_t);   \
+  template bool launch_lincomb_dot<T>(const Geo &, cplx<T> *, int, const cplx<T> *, int, const double *, int, const double *, \
+                                      double, const cplx<T> *, double *, cudaStream_t);                              \
   template void launch_axpby<T>(const Geo &, cplx<T> *, const cplx<T> *, int, double, double, cudaStream_t);          \
   template void launch_scale_rows<T>(const Geo &, cplx<T> *, const double *, int, cudaStream_t);                      \
   template void launch_tpa_table<T>(const Geo &, T *, const double *, int, cudaStream_t);                            \

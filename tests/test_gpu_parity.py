@@ -158,6 +158,24 @@ def test_pdep_matches_dense_eigenvalues():
     assert np.abs(chi @ q.T - q.T * lam[None, :]).max() < 1e-7
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed_df"])
+def test_pdep_small_system_matches_dense_eigenvalues(prec):
+    # s and p projectors, 895 plane waves; 8 lowest eigenpairs from a 12-vector start block
+    s = synth.make_system("small")
+    H = hamiltonian.Hamiltonian(s)
+    wa, pa = H.all_states()
+    chi = dfpt.adler_wiser_chi0bar(H, wa, pa, s.nocc)
+    neig = 8
+    ref = pdep.dense_eigs(chi, neig)
+    guess = synth.make_perturbations(s, 12, 4)
+    with wdf.Context(s, precision=prec, cg_tol=1e-12, gs_tol=1e-11) as c:
+        lam, vec, st = c.pdep(neig, guess, maxiter=100, tol=1e-9)
+    assert st.converged == 1
+    assert np.abs(lam - ref).max() / np.abs(ref).max() < 1e-8
+    q = basis.half_to_real(vec)[:, 1:]
+    assert np.abs(q @ q.T - np.eye(neig)).max() < 1e-10
+
+
 def test_deterministic_and_device_pointers():
     import torch
 
