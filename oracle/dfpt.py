@@ -80,8 +80,15 @@ class Response:
         prod = dv_r * self.psi_r[vidx]
         return -self.project_q(basis.to_sphere(prod, self.H.miller, self.H.grid))
 
+    def tpa_rows(self, vidx):
+        """TPA preconditioner K(1/2 |G|^2 / T_v) for the orbital of each row (full sphere)."""
+        return tpa(0.5 * self.H.g2[None, :] / self.tkin[np.asarray(vidx)][:, None])
+
     def sternheimer(self, b, vidx, tol=1e-13, maxiter=5000, precondition=True):
         """Solve A_v d = b row by row by preconditioned CG (FP64).
+
+        ``precondition``: True for TPA, False for none, or an array of diagonal preconditioner
+        values (rows x plane waves), e.g. a learned scale times TPA.
 
         Stops a row when the recursive residual satisfies ||r|| <= tol ||b||, then recomputes
         the true residual b - A d; rows whose true residual is still above tol restart from the
@@ -90,7 +97,12 @@ class Response:
         b = np.asarray(b, dtype=np.complex128)
         nrow = b.shape[0]
         eps_rows = self.eps[vidx]
-        kprec = tpa(0.5 * self.H.g2[None, :] / self.tkin[vidx][:, None]) if precondition else np.ones((nrow, b.shape[1]))
+        if isinstance(precondition, np.ndarray):  # an explicit diagonal preconditioner per row
+            kprec = np.broadcast_to(np.asarray(precondition, dtype=np.float64), b.shape)
+        elif precondition:
+            kprec = self.tpa_rows(vidx)
+        else:
+            kprec = np.ones((nrow, b.shape[1]))
         bnorm = np.sqrt(np.real(basis.dot(b, b)))
         bnorm = np.where(bnorm > 0, bnorm, 1.0)
         d = np.zeros_like(b)
