@@ -21,6 +21,7 @@ each rank runs its own block (weak scaling) and rank 0 reports the total.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -40,8 +41,31 @@ WORKLOAD = "medium"
 NPERT = 128
 NEIG = 64
 METRIC = "sternheimer_solves_per_s_at_1e-8"
-# kernel class timed for the roofline, per precision: (class, bound)
-ROOFLINE_KERNEL = {"mixed_df": ("plane_vloc:32", "hbm"), "mixed": ("plane_vloc:32", "hbm"), "fp64": ("plane_vloc:64", "hbm")}
+# kernel class timed for the roofline, per precision: (class, bound). The per-plane FFT kernel
+# keeps its data on chip (its HBM traffic is the column buffer only): its limit is arithmetic.
+ROOFLINE_KERNEL = {"mixed_df": ("plane_vloc:32", "alu"), "mixed": ("plane_vloc:32", "alu"), "fp64": ("plane_vloc:64", "alu")}
+# arithmetic peaks: FP32 from unit counts and clock (152 SMs x 128 lanes x 2 flop x 2.07 GHz);
+# FP64 from a measured FMA loop on this GPU (the FP64 unit count is not published)
+ALU_PEAK_TFLOPS = {"mixed_df": 152 * 128 * 2 * 2.07e9 / 1e12, "mixed": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 1.19}
+ALU_PEAK_SOURCE = {"mixed_df": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                   "mixed": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                   "fp64": "FP64: measured FMA loop on GB300, 1.19 TFLOP/s"}
+
+
+def plane_flops(system, npair: int) -> float:
+    """FFT flops (5 n log2 n per complex line) of one V_loc plane launch over npair pairs.
+
+    Per pair and z plane: n2 inverse transforms of the occupied n1 columns, n1 inverse transforms
+    of every row, the real V_loc product, and the same transforms forward.
+    """
+    import math
+
+    n1, n2, n3 = system.grid
+    full = np.concatenate([system.miller, -system.miller[1:]])
+    nx = len({int(a) % n1 for a in full[:, 0]})
+    line = lambda n: 5.0 * n * math.log2(n)  # noqa: E731
+    per_plane = 2.0 * (nx * line(n2) + n2 * line(n1)) + 2.0 * n1 * n2
+    return per_plane * n3 * npair
 UNIT = "solves/s"
 
 
@@ -199,6 +223,20 @@ def run_gpu(args):
                       max_batch=args.max_batch)
     t_setup = time.perf_counter() - t_setup
     eps, _ = ctx.orbitals()
+    train_info = None
+    if args.precond == "learned":
+        # train on other seeds of the same system family (the benchmarked system is seed 0)
+        t_tr = time.perf_counter()
+        fam = [wdf.Context(synth.make_system(dataclasses.replace(synth.spec(WORKLOAD), seed=k)), precision=args.precision, cg_tol=1e-8,
+                           stream=stream.cuda_stream, device=local) for k in range(1, args.train_systems + 1)]
+        model, ts = wdf.train_preconditioner(fam, npert=args.train_npert, steps=args.train_steps, seed=12345)
+        for c in fam:
+            c.close()
+        ctx.set_model(model)
+        train_info = {"systems": f"{WORKLOAD} family, seeds 1..{args.train_systems} (benchmarked system: seed 0)",
+                      "perturbations_per_system": args.train_npert, "samples": ts.nsamples, "adam_steps": ts.steps,
+                      "loss_first": ts.loss_first, "loss_last": ts.loss_last, "train_ms": ts.ms,
+                      "wall_s_incl_ground_states": time.perf_counter() - t_tr}
     phi_d = torch.from_numpy(phi_h).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -265,39 +303,40 @@ def run_gpu(args):
     if rank != 0:
         return
     hbm, bf16, src = peaks()
-    # algorithmic bytes of one launch of the dominant kernel (kernels table)
-    sc = 16 if args.precision == "fp64" else 8
-    full = np.concatenate([s.miller, -s.miller[1:]])
-    ndisk = len({(int(a), int(b)) for a, b, _ in full})
-    n1, n2, n3 = s.grid
+    # algorithmic flops of one launch of the dominant kernel (FFT convention)
     npair = NPERT * s.nocc // 2
-    per_launch_bytes = npair * n3 * 2 * ndisk * sc + n1 * n2 * n3 * sc // 2
+    per_launch_flops = plane_flops(s, npair)
     avg_ms = k_ms / max(1, k_launches)
-    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if k_launches else None
+    achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12 if k_launches else None
+    alu_peak = ALU_PEAK_TFLOPS[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed": "f32+f64", "mixed_df": "f32+df64+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": "medium: L=20 bohr, 64^3 grid, |G|^2<=25, 8440 stored PWs, 32 atoms (128 KB projectors), "
                                "64 occupied, 128 perturbations per GPU, PDEP 64 eigenpairs, one Davidson iteration per step",
-                   "precision": args.precision, "cg_tol": 1e-8, "l2": "flushed (256 MiB write) before each step; working set > L2",
+                   "precision": args.precision, "precond": args.precond, "cg_tol": 1e-8,
+                   "l2": "flushed (256 MiB write) before each step; working set > L2",
                    "parallelism": f"perturbation blocks x{world}"},
         "chi0_applies_per_s": job_throughput(world, NPERT, ms_dev),
         "cg_iters_per_solve": iters,
         "max_residual": stats[-1]["max_residual"],
+        "fallbacks_per_step": stats[-1]["fallbacks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,
                 "d2h_bytes_per_step": NEIG * s.npw_h * 16 + NEIG * 8},
         "gpu_launches": int(round(launches)),
-        "roofline": {"kernel": target, "bound": bound, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+        "roofline": {"kernel": target, "bound": bound, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
                      "launches_per_step": k_launches / args.steps, "ms_per_launch": avg_ms,
-                     "share_of_step": k_ms / args.steps / ms_dev, "algorithmic_bytes_per_launch": per_launch_bytes,
-                     "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                     "share_of_step": k_ms / args.steps / ms_dev, "algorithmic_flops_per_launch": per_launch_flops,
+                     "peak_source": ALU_PEAK_SOURCE[args.precision]},
         "clocks": clocks,
         "peaks_source": src,
         "setup_s": t_setup,
         "eps_homo": float(eps[-1]),
     }
+    if train_info:
+        line["learned_preconditioner"] = train_info
     if args.cpu_baseline:
         sys_o, R, phi1, t_gs = oracle_sample(WORKLOAD)
         t0 = time.time()
@@ -317,12 +356,17 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["wdf", "reference"], default="wdf")
-    ap.add_argument("--precision", choices=["mixed_df", "mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed_df", "mixed", "fp64"], default="mixed_df")
     ap.add_argument("--max-batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true", help="one warm step, then one step between "
                     "cudaProfilerStart/Stop for ncu --profile-from-start off; no timing line")
     ap.add_argument("--npert", type=int, default=128, help="perturbations per block (default 128)")
+    ap.add_argument("--precond", choices=["tpa", "learned"], default="tpa",
+                    help="learned: train the MLP preconditioner on other seeds of the family first (not timed)")
+    ap.add_argument("--train-systems", type=int, default=4)
+    ap.add_argument("--train-npert", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=600)
     args = ap.parse_args()
     global NPERT, NEIG
     NPERT = args.npert

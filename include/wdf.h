@@ -63,7 +63,10 @@ enum wdf_mem { WDF_MEM_HOST = 0, WDF_MEM_DEVICE = 1 };
  *   stay FP64. GB300 issues FP32 about 60 times faster than FP64. */
 enum wdf_precision { WDF_FP64 = 0, WDF_MIXED = 1, WDF_MIXED_DF = 2 };
 
-enum wdf_precond { WDF_PRECOND_NONE = 0, WDF_PRECOND_TPA = 1 };
+/* Preconditioner of the Sternheimer CG. WDF_PRECOND_TPA: Teter-Payne-Allan, K(x) with
+ * x = (1/2 |G|^2) / T_v. WDF_PRECOND_LEARNED: s(v, G) K, s from a trained model (wdf_set_model);
+ * a solve whose residual norm falls by less than 10% over 5 iterations restarts with TPA. */
+enum wdf_precond { WDF_PRECOND_NONE = 0, WDF_PRECOND_TPA = 1, WDF_PRECOND_LEARNED = 2 };
 
 typedef struct wdf_ctx wdf_ctx;
 
@@ -100,6 +103,8 @@ typedef struct wdf_options {
   int gs_extra;      /* ground state: extra states beyond nocc carried in the Davidson (default 8) */
   void *stream;      /* cudaStream_t for all work of the context (NULL: default stream) */
   int device;        /* CUDA device ordinal (default 0) */
+  int warm_start;    /* WDF_PRECOND_LEARNED: start each solve from the model's first iterate
+                        x0 = o1(v, G) K b instead of 0 (default 0) */
 } wdf_options;
 
 /* Statistics of the last apply / Davidson call. */
@@ -113,6 +118,7 @@ typedef struct wdf_stats {
   int32_t davidson_iters;  /* Davidson iterations */
   int32_t converged;       /* 1 if every requested quantity met its tolerance */
   double ms;               /* wall time of the call, milliseconds */
+  int32_t fallbacks;       /* WDF_PRECOND_LEARNED: solves that stalled and restarted with TPA */
 } wdf_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -189,6 +195,84 @@ int wdf_pdep_davidson(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, doubl
  * Errors: WDF_EINVAL, WDF_ECUDA, WDF_ESTATE. */
 int wdf_apply_hamiltonian_noalloc(wdf_ctx *ctx, int nvec, const double *in, double *out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned Sternheimer preconditioner. The paper has no counterpart: it is an extension that
+ * keeps the method's result (the converged solves) and changes only the CG path to it.
+ *
+ * Model: a multilayer perceptron 4 -> 64 -> 64 -> 2 (tanh hidden layers) evaluated per occupied
+ * orbital v and plane wave G on the features
+ *   f0 = log(1 + (1/2 |G|^2) / T_v), f1 = eps_v, f2 = T_v, f3 = log(npw_h |c_v(G)|^2 + 1e-6),
+ * normalised as (f - mu) / sd; T_v is the kinetic energy of psi_v. Output o0 gives the diagonal
+ * scale s = exp(o0) (o0 clamped to [-8, 8]) of the preconditioner s K_TPA; output o1 the first
+ * iterate x0 = o1 K_TPA b.
+ * Training samples come from converged TPA solves of chi0bar applications: per (v, G), summed
+ * over the solves of orbital v, E_x = sum |x|^2, E_k = sum |K b|^2, C = sum Re(conj(K b) x);
+ * targets t0 = 1/2 log(E_x / E_k), t1 = C / E_k; weights w0 ~ E_x + E_k, w1 ~ E_k counted for G
+ * and -G and normalised to unit sum per call. Loss sum_i sum_k w_ik (o_ik - t_ik)^2; full-batch
+ * Adam (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) by the library's own kernels.
+ * Weights: WDF_MODEL_FLOATS floats W1[4][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]
+ * (the WDF_MODEL_NPARAM trained values), then mu[4], sd[4].
+ * Samples: features [n][4], targets [n][2], weights [n][2], floats.
+ * A model lives on one GPU and is used by one thread at a time. */
+typedef struct wdf_model wdf_model;
+#define WDF_MODEL_NPARAM 4610
+#define WDF_MODEL_FLOATS 4618
+
+typedef struct wdf_train_opts {
+  int steps;       /* full-batch Adam steps per wdf_model_train call (default 600) */
+  double lr;       /* Adam learning rate (default 3e-3) */
+  int npert;       /* wdf_train_preconditioner: perturbations per context (default 8) */
+  uint64_t seed;   /* wdf_train_preconditioner: seed of the perturbations and initial weights */
+} wdf_train_opts;
+
+typedef struct wdf_train_stats {
+  int64_t nsamples;   /* samples in the model */
+  int32_t steps;      /* Adam steps taken by the call */
+  double loss_first;  /* loss before the first step of the call */
+  double loss_last;   /* loss before the last step of the call */
+  double ms;          /* wall time of the call, milliseconds */
+} wdf_train_stats;
+
+void wdf_default_train_opts(wdf_train_opts *opt);
+
+/* New model on CUDA device `device`: weights drawn from splitmix64(seed) (normal, variance
+ * 1/fan-in; biases 0), mu = 0, sd = 1, no samples. The first wdf_model_train call of a model
+ * created this way sets mu, sd from the samples and b3 to the weighted target means.
+ * Errors: WDF_EINVAL, WDF_ENOMEM, WDF_ECUDA, WDF_ESTATE. */
+int wdf_model_create(int device, uint64_t seed, wdf_model **out);
+/* Release a model (NULL is ignored). */
+void wdf_model_free(wdf_model *m);
+/* Replace / read the WDF_MODEL_FLOATS weights (host). Setting weights keeps mu and sd as given
+ * and resets the Adam moments. */
+int wdf_model_set_weights(wdf_model *m, const float *w);
+int wdf_model_get_weights(const wdf_model *m, float *w);
+/* Apply chi0bar to npert perturbations phi ([npert][npw_h] complex, host or device per mem) with
+ * TPA solves to the context's cg_tol and append the nocc * npw_h samples of those solves, in the
+ * order (v, half-sphere index). The model must live on the context's GPU. st: optional stats of
+ * the chi0bar application. Errors: as wdf_apply_chi0. */
+int wdf_model_add_solves(wdf_model *m, wdf_ctx *ctx, int npert, const double *phi, int mem, wdf_stats *st);
+/* Number of samples (-1 for NULL). */
+int64_t wdf_model_num_samples(const wdf_model *m);
+/* Replace all samples by n given ones / read count samples from index first (host arrays). */
+int wdf_model_set_samples(wdf_model *m, int64_t n, const float *feat, const float *tgt, const float *wt);
+int wdf_model_get_samples(const wdf_model *m, int64_t first, int64_t count, float *feat, float *tgt, float *wt);
+/* Loss over all samples and its gradient grad[WDF_MODEL_NPARAM] (host) at the current weights. */
+int wdf_model_loss_grad(wdf_model *m, double *loss, double *grad);
+/* opt->steps full-batch Adam steps on the samples (opt NULL: defaults). Errors: WDF_EINVAL (no
+ * samples), WDF_ENAN (non-finite loss). */
+int wdf_model_train(wdf_model *m, const wdf_train_opts *opt, wdf_train_stats *st);
+/* Outputs out[n][2] = (o0, o1) for raw features feat[n][4] (host). */
+int wdf_model_predict(wdf_model *m, int64_t n, const float *feat, float *out);
+/* Evaluate the model for every (v, G) of the context, store s K_TPA and o1 K_TPA, and switch the
+ * context to WDF_PRECOND_LEARNED. m NULL: back to WDF_PRECOND_TPA. The model must live on the
+ * context's GPU; the context keeps no reference to it. */
+int wdf_set_model(wdf_ctx *ctx, const wdf_model *m);
+/* Convenience: create a model from opt->seed, add the solves of opt->npert perturbations drawn
+ * from splitmix64(opt->seed) (Gaussian coefficients, G = 0 removed, unit norm) for each of the n
+ * contexts, and train it. *out receives the model (NULL on failure). */
+int wdf_train_preconditioner(wdf_ctx *const *ctx, int n, const wdf_train_opts *opt, wdf_model **out,
+                             wdf_train_stats *st);
+
 /* Instrumentation: time one kernel class with CUDA events. Every later launch of that class made
  * by calls on ctx is bracketed by two events recorded on the stream it is launched on.
  * kernel: a class name, optionally with ":64", ":32" or ":48" for the precision, e.g. "plane_vloc:32".
@@ -196,7 +280,7 @@ int wdf_apply_hamiltonian_noalloc(wdf_ctx *ctx, int nvec, const double *in, doub
  * lincomb, dot_partial, cg_start, cg_update, cg_direction, cg_scalars, axpby, scale_rows,
  * convert, ext_to_int, int_to_ext, ritz_residual, tpa_table, kinetic, mul_table, check_finite,
  * jac_init, jac_rows, jac_cols, jac_check, jac_sort, split_pairs, scale_elems, gather_shift,
- * sum_chunks. NULL stops timing. Calling it resets the counters. Errors: WDF_EINVAL. */
+ * sum_chunks, chol_inv, mlp_grad, mlp_reduce, mlp_adam, mlp_table, mlp_accum, mlp_samples. NULL stops timing. Calling it resets the counters. Errors: WDF_EINVAL. */
 int wdf_profile_kernel(wdf_ctx *ctx, const char *kernel);
 
 /* Launches of the selected class since wdf_profile_kernel and their summed device time in

@@ -4,6 +4,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
+#include <algorithm>
 
 #include "engine.cuh"
 
@@ -127,6 +129,7 @@ void fill_stats(wdf_stats *st, const SolveStats &ss, long long nsolve, long long
   st->napply = napply;
   st->converged = ss.converged ? 1 : 0;
   st->ms = ms;
+  st->fallbacks = ss.fallbacks;
 }
 
 void setup_body(wdf_ctx *c, const wdf_system *sys) {
@@ -243,6 +246,9 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   set_fft_smem_limits<double>(g);
   set_fft_smem_limits<float>(g);
   set_fft_smem_limits<df64>(g);
+  set_chol_inv_limits(kCholMax);
+  set_mlp_limits();
+  if (tc_enabled()) set_tc_limits();
 
   // local potential
   c->vloc64.ensure(sizeof(double) * c->ngrid);
@@ -308,6 +314,7 @@ struct Chi0Op : DavOp {
     agg.refinements = std::max(agg.refinements, ss.refinements);
     agg.max_res = std::max(agg.max_res, ss.max_res);
     agg.converged = agg.converged && ss.converged;
+    agg.fallbacks += ss.fallbacks;
     nsolve += (long long)n * c->nocc;
   }
 };
@@ -394,11 +401,13 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->dv_H,      &c->dv_Y,      &c->dv_theta, &c->dv_jac, &c->dv_jint, &c->dv_small, &c->dv_neg,   &c->zeros,
                   &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho, &c->t_xactn, &c->t_jidx,
                   &c->t_twdf,    &c->vlocdf,    &c->Udf,     &c->psirdf,   &c->dfa,     &c->dfb,
-                  &c->xpdf,      &c->dvgriddf,  &c->accgriddf, &c->cb2df,  &c->drdf,    &c->oudf};
+                  &c->xpdf,      &c->dvgriddf,  &c->accgriddf, &c->cb2df,  &c->drdf,    &c->oudf, &c->chol,
+                  &c->ml64,      &c->ml32,      &c->mlw64,   &c->krow,     &c->rr_ref,  &c->it_ref,  &c->nfb,
+                  &c->mlsums,    &c->mlwraw,    &c->tcU,     &c->tcUt,     &c->tcC,     &c->tcerr};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {
-    DBuf *cb[] = {&w->r, &w->z, &w->p, &w->Ap, &w->x, &w->cb, &w->S, &w->part1, &w->part2, &w->dbl, &w->ints};
+    DBuf *cb[] = {&w->r, &w->z, &w->p, &w->Ap, &w->x, &w->cb, &w->S, &w->part1, &w->part2, &w->part3, &w->dbl, &w->ints};
     for (DBuf *b : cb) b->release();
   }
   delete c;
@@ -559,5 +568,420 @@ const char *wdf_strerror(int s) {
 const char *wdf_last_error(const wdf_ctx *c) { return c ? c->err.c_str() : last_global_error(); }
 
 const char *wdf_version(void) { return "wdf 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// learned preconditioner models
+
+namespace {
+
+// splitmix64 (Steele, Lea and Flood, OOPSLA 2014): state += golden gamma, then the variant-13
+// finaliser; output k of seed s is the finaliser of s + (k + 1) gamma
+uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// uniform in (0, 1) from the top 53 bits
+double unit_open(uint64_t x) { return ((double)(x >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+// standard normal number k of a stream (Box-Muller on two consecutive outputs)
+double normal_at(uint64_t seed, uint64_t k) {
+  const double u1 = unit_open(splitmix64(seed, 2 * k)), u2 = unit_open(splitmix64(seed, 2 * k + 1));
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+template <class F> int mguard(wdf_model *m, F &&body) {
+  try {
+    cudaError_t e = cudaSetDevice(m->device);
+    if (e != cudaSuccess) throw CudaFailure(e, "cudaSetDevice", __FILE__, __LINE__);
+    return body();
+  } catch (const ApiFailure &f) {
+    m->err = f.msg;
+    set_error(f.code, f.msg);
+    return f.code;
+  } catch (const CudaFailure &f) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(f.err), cudaGetErrorString(f.err), f.what,
+             f.file, f.line);
+    m->err = buf;
+    set_error(WDF_ECUDA, buf);
+    return WDF_ECUDA;
+  } catch (const std::bad_alloc &) {
+    set_error(WDF_ENOMEM, "host allocation failed");
+    return WDF_ENOMEM;
+  } catch (...) {
+    set_error(WDF_EINVAL, "unexpected C++ exception");
+    return WDF_EINVAL;
+  }
+}
+
+// grow a buffer keeping its first `used` bytes
+void grow_keep(DBuf &b, size_t used, size_t need) {
+  if (need <= b.cap) return;
+  DBuf nb;
+  nb.ensure(std::max(need, 2 * b.cap));
+  if (used) WDF_CUDA_TRY(cudaMemcpy(nb.p, b.p, used, cudaMemcpyDeviceToDevice));
+  b.release();
+  b = nb;
+}
+
+void model_reserve(wdf_model *m, long long n) {
+  if (n <= m->cap) return;
+  const long long cap = std::max<long long>(n, 2 * m->cap);
+  grow_keep(m->feat, sizeof(float) * 4 * m->n, sizeof(float) * 4 * cap);
+  grow_keep(m->tgt, sizeof(float) * 2 * m->n, sizeof(float) * 2 * cap);
+  grow_keep(m->wt, sizeof(float) * 2 * m->n, sizeof(float) * 2 * cap);
+  m->cap = cap;
+}
+
+void model_upload(wdf_model *m, const std::vector<double> &w) {
+  std::vector<float> f(w.begin(), w.end());
+  WDF_CUDA_TRY(cudaMemcpy(m->w64.p, w.data(), sizeof(double) * kMlpFloats, cudaMemcpyHostToDevice));
+  WDF_CUDA_TRY(cudaMemcpy(m->w32.p, f.data(), sizeof(float) * kMlpFloats, cudaMemcpyHostToDevice));
+  WDF_CUDA_TRY(cudaMemset(m->m.p, 0, sizeof(double) * kMlpParams));
+  WDF_CUDA_TRY(cudaMemset(m->v.p, 0, sizeof(double) * kMlpParams));
+  m->t = 0;
+}
+
+// loss and gradient at the current weights into m->grad (device)
+void model_grad(wdf_model *m) {
+  set_mlp_limits();
+  m->part.ensure(sizeof(double) * (kMlpParams + 1) * (size_t)mlp_grad_blocks(m->n));
+  launch_mlp_grad(m->w32.as<float>(), m->feat.as<float>(), m->tgt.as<float>(), m->wt.as<float>(), m->n, m->part.as<double>(),
+                  m->grad.as<double>(), 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+void wdf_default_train_opts(wdf_train_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->steps = 600;
+  o->lr = 3e-3;
+  o->npert = 8;
+  o->seed = 0;
+}
+
+int wdf_model_create(int device, uint64_t seed, wdf_model **out) {
+  if (!out) {
+    set_error(WDF_EINVAL, "out must not be NULL");
+    return WDF_EINVAL;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    set_error(WDF_ESTATE, "no CUDA device available");
+    return WDF_ESTATE;
+  }
+  if (device < 0 || device >= ndev) {
+    set_error(WDF_EINVAL, "device ordinal out of range");
+    return WDF_EINVAL;
+  }
+  wdf_model *m = new (std::nothrow) wdf_model();
+  if (!m) {
+    set_error(WDF_ENOMEM, "host allocation failed");
+    return WDF_ENOMEM;
+  }
+  m->device = device;
+  const int rc = mguard(m, [&] {
+    m->w64.ensure(sizeof(double) * kMlpFloats);
+    m->w32.ensure(sizeof(float) * kMlpFloats);
+    m->m.ensure(sizeof(double) * kMlpParams);
+    m->v.ensure(sizeof(double) * kMlpParams);
+    m->grad.ensure(sizeof(double) * (kMlpParams + 1));
+    // weights: normal with variance 1 / fan-in (4, 64, 64); biases 0; mu 0, sd 1
+    std::vector<double> w(kMlpFloats, 0.0);
+    const int fan_off[3][3] = {{0, 256, 4}, {320, 4096, 64}, {4480, 128, 64}};
+    uint64_t k = 0;
+    for (auto &L : fan_off)
+      for (int i = 0; i < L[1]; ++i) w[L[0] + i] = normal_at(seed, k++) / std::sqrt((double)L[2]);
+    for (int i = 0; i < 4; ++i) w[kMlpParams + 4 + i] = 1.0;
+    model_upload(m, w);
+    m->fresh = true;
+    return WDF_OK;
+  });
+  if (rc != WDF_OK) {
+    wdf_model_free(m);
+    return rc;
+  }
+  *out = m;
+  return WDF_OK;
+}
+
+void wdf_model_free(wdf_model *m) {
+  if (!m) return;
+  (void)cudaSetDevice(m->device);
+  (void)cudaDeviceSynchronize();
+  for (DBuf *b : {&m->w64, &m->w32, &m->m, &m->v, &m->grad, &m->part, &m->feat, &m->tgt, &m->wt, &m->pin, &m->pout}) b->release();
+  delete m;
+}
+
+int wdf_model_set_weights(wdf_model *m, const float *w) {
+  if (!m || !w) return WDF_EINVAL;
+  return mguard(m, [&] {
+    std::vector<double> d(w, w + kMlpFloats);
+    for (int i = 0; i < 4; ++i)
+      if (!(d[kMlpParams + 4 + i] > 0)) throw ApiFailure(WDF_EINVAL, "sd entries must be positive");
+    for (double x : d)
+      if (!std::isfinite(x)) throw ApiFailure(WDF_ENAN, "non-finite weight");
+    model_upload(m, d);
+    m->fresh = false;
+    return WDF_OK;
+  });
+}
+
+int wdf_model_get_weights(const wdf_model *mc, float *w) {
+  wdf_model *m = const_cast<wdf_model *>(mc);
+  if (!m || !w) return WDF_EINVAL;
+  return mguard(m, [&] {
+    WDF_CUDA_TRY(cudaMemcpy(w, m->w32.p, sizeof(float) * kMlpFloats, cudaMemcpyDeviceToHost));
+    return WDF_OK;
+  });
+}
+
+int64_t wdf_model_num_samples(const wdf_model *m) { return m ? (int64_t)m->n : -1; }
+
+int wdf_model_set_samples(wdf_model *m, int64_t n, const float *feat, const float *tgt, const float *wt) {
+  if (!m || n < 0 || (n > 0 && (!feat || !tgt || !wt))) return WDF_EINVAL;
+  return mguard(m, [&] {
+    m->n = 0;
+    model_reserve(m, n);
+    if (n > 0) {
+      WDF_CUDA_TRY(cudaMemcpy(m->feat.p, feat, sizeof(float) * 4 * n, cudaMemcpyHostToDevice));
+      WDF_CUDA_TRY(cudaMemcpy(m->tgt.p, tgt, sizeof(float) * 2 * n, cudaMemcpyHostToDevice));
+      WDF_CUDA_TRY(cudaMemcpy(m->wt.p, wt, sizeof(float) * 2 * n, cudaMemcpyHostToDevice));
+    }
+    m->n = n;
+    return WDF_OK;
+  });
+}
+
+int wdf_model_get_samples(const wdf_model *mc, int64_t first, int64_t count, float *feat, float *tgt, float *wt) {
+  wdf_model *m = const_cast<wdf_model *>(mc);
+  if (!m || first < 0 || count < 0 || first + count > m->n) return WDF_EINVAL;
+  return mguard(m, [&] {
+    if (count == 0) return WDF_OK;
+    if (feat) WDF_CUDA_TRY(cudaMemcpy(feat, m->feat.as<float>() + 4 * first, sizeof(float) * 4 * count, cudaMemcpyDeviceToHost));
+    if (tgt) WDF_CUDA_TRY(cudaMemcpy(tgt, m->tgt.as<float>() + 2 * first, sizeof(float) * 2 * count, cudaMemcpyDeviceToHost));
+    if (wt) WDF_CUDA_TRY(cudaMemcpy(wt, m->wt.as<float>() + 2 * first, sizeof(float) * 2 * count, cudaMemcpyDeviceToHost));
+    return WDF_OK;
+  });
+}
+
+int wdf_model_add_solves(wdf_model *m, wdf_ctx *c, int npert, const double *phi, int mem, wdf_stats *st) {
+  if (!m || !c) return WDF_EINVAL;
+  if (m->device != c->device) {
+    set_error(WDF_EINVAL, "the model and the context live on different GPUs");
+    return WDF_EINVAL;
+  }
+  return guarded(c, [&] {
+    Timer tm;
+    check_mem(mem);
+    if (npert < 1 || !phi) throw ApiFailure(WDF_EINVAL, "bad npert or NULL phi");
+    const Geo &g = c->geo;
+    cplx<double> *P = read_in(c, c->ext_in, c->guess, phi, npert, mem, 1);
+    const int np2 = 2 * ((npert + 1) / 2);
+    c->outi.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+    c->drhoi.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
+    c->mlsums.ensure(sizeof(double) * 3 * (size_t)c->nocc * g.ld);
+    WDF_CUDA_TRY(cudaMemsetAsync(c->mlsums.p, 0, sizeof(double) * 3 * (size_t)c->nocc * g.ld, c->st));
+    // TPA solves with the sums collected; the options come back whatever happens
+    struct Restore {
+      wdf_ctx *c;
+      int precond;
+      ~Restore() {
+        c->opt.precond = precond;
+        c->collect = false;
+      }
+    } restore{c, c->opt.precond};
+    c->opt.precond = WDF_PRECOND_TPA;
+    c->collect = true;
+    SolveStats ss;
+    chi0_apply_internal(c, P, npert, c->outi.as<cplx<double>>(), c->drhoi.as<cplx<double>>(), ss);
+    const long long add = (long long)c->nocc * c->npw_h;
+    model_reserve(m, m->n + add);
+    c->mlwraw.ensure(sizeof(double) * (2 * (size_t)add + 2));
+    double *wraw = c->mlwraw.as<double>();
+    launch_mlp_samples(g, c->t_emap.as<int>(), c->npw_h, c->nocc, c->mlsums.as<double>(),
+                       c->U64.as<cplx<double>>() + (size_t)c->nproj * g.ld, c->tkin.as<double>(), c->eps_dev.as<double>(),
+                       m->feat.as<float>() + 4 * m->n, m->tgt.as<float>() + 2 * m->n, m->wt.as<float>() + 2 * m->n, wraw,
+                       wraw + 2 * add, c->st);
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    m->n += add;
+    fill_stats(st, ss, (long long)npert * c->nocc, npert, tm.ms());
+    return ss.converged ? WDF_OK : WDF_ENOCONV;
+  });
+}
+
+int wdf_model_loss_grad(wdf_model *m, double *loss, double *grad) {
+  if (!m || !loss || !grad) return WDF_EINVAL;
+  return mguard(m, [&] {
+    if (m->n == 0) throw ApiFailure(WDF_EINVAL, "the model has no samples");
+    model_grad(m);
+    std::vector<double> h(kMlpParams + 1);
+    WDF_CUDA_TRY(cudaMemcpy(h.data(), m->grad.p, sizeof(double) * (kMlpParams + 1), cudaMemcpyDeviceToHost));
+    std::copy(h.begin(), h.begin() + kMlpParams, grad);
+    *loss = h[kMlpParams];
+    return WDF_OK;
+  });
+}
+
+int wdf_model_train(wdf_model *m, const wdf_train_opts *opt, wdf_train_stats *st) {
+  if (!m) return WDF_EINVAL;
+  wdf_train_opts o;
+  if (opt) o = *opt;
+  else wdf_default_train_opts(&o);
+  return mguard(m, [&] {
+    auto t0 = std::chrono::steady_clock::now();
+    if (m->n == 0) throw ApiFailure(WDF_EINVAL, "the model has no samples");
+    if (o.steps < 0 || !(o.lr > 0)) throw ApiFailure(WDF_EINVAL, "bad training options");
+    if (m->fresh && m->t == 0) {
+      // feature normalisation and output biases from the samples (host, FP64)
+      const long long n = m->n;
+      std::vector<float> f(4 * n), t(2 * n), w(2 * n);
+      WDF_CUDA_TRY(cudaMemcpy(f.data(), m->feat.p, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost));
+      WDF_CUDA_TRY(cudaMemcpy(t.data(), m->tgt.p, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
+      WDF_CUDA_TRY(cudaMemcpy(w.data(), m->wt.p, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
+      std::vector<double> wd(kMlpFloats);
+      WDF_CUDA_TRY(cudaMemcpy(wd.data(), m->w64.p, sizeof(double) * kMlpFloats, cudaMemcpyDeviceToHost));
+      for (int k = 0; k < 4; ++k) {
+        double s1 = 0.0, s2 = 0.0;
+        for (long long i = 0; i < n; ++i) s1 += f[4 * i + k];
+        const double mu = s1 / (double)n;
+        for (long long i = 0; i < n; ++i) s2 += (f[4 * i + k] - mu) * (f[4 * i + k] - mu);
+        const double sd = std::sqrt(s2 / (double)n);
+        wd[kMlpParams + k] = mu;
+        wd[kMlpParams + 4 + k] = sd > 1e-6 ? sd : 1.0;
+      }
+      for (int k = 0; k < 2; ++k) {
+        double sw = 0.0, st2 = 0.0;
+        for (long long i = 0; i < n; ++i) {
+          sw += w[2 * i + k];
+          st2 += (double)w[2 * i + k] * t[2 * i + k];
+        }
+        wd[kMlpParams - 2 + k] = sw > 0 ? st2 / sw : 0.0;
+      }
+      model_upload(m, wd);
+    }
+    double first = 0.0, last = 0.0;
+    for (int s = 0; s < o.steps; ++s) {
+      model_grad(m);
+      if (s == 0 || s == o.steps - 1) {
+        double l = 0.0;
+        WDF_CUDA_TRY(cudaMemcpy(&l, m->grad.as<double>() + kMlpParams, sizeof(double), cudaMemcpyDeviceToHost));
+        if (!std::isfinite(l)) throw ApiFailure(WDF_ENAN, "non-finite training loss");
+        if (s == 0) first = l;
+        last = l;
+      }
+      launch_mlp_adam(m->w64.as<double>(), m->w32.as<float>(), m->grad.as<double>(), m->m.as<double>(), m->v.as<double>(), ++m->t,
+                      o.lr, 0);
+    }
+    WDF_CUDA_TRY(cudaDeviceSynchronize());
+    m->fresh = false;
+    if (st) {
+      st->nsamples = m->n;
+      st->steps = o.steps;
+      st->loss_first = first;
+      st->loss_last = last;
+      st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return WDF_OK;
+  });
+}
+
+int wdf_model_predict(wdf_model *m, int64_t n, const float *feat, float *out) {
+  if (!m || n < 0 || (n > 0 && (!feat || !out))) return WDF_EINVAL;
+  return mguard(m, [&] {
+    if (n == 0) return WDF_OK;
+    m->pin.ensure(sizeof(float) * 4 * n);
+    m->pout.ensure(sizeof(float) * 2 * n);
+    WDF_CUDA_TRY(cudaMemcpy(m->pin.p, feat, sizeof(float) * 4 * n, cudaMemcpyHostToDevice));
+    launch_mlp_predict(m->w32.as<float>(), m->pin.as<float>(), n, m->pout.as<float>(), 0);
+    WDF_CUDA_TRY(cudaMemcpy(out, m->pout.p, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
+    return WDF_OK;
+  });
+}
+
+int wdf_set_model(wdf_ctx *c, const wdf_model *m) {
+  if (!c) return WDF_EINVAL;
+  return guarded(c, [&] {
+    if (!m) {
+      c->opt.precond = WDF_PRECOND_TPA;
+      c->has_model = false;
+      return WDF_OK;
+    }
+    if (m->device != c->device) throw ApiFailure(WDF_EINVAL, "the model and the context live on different GPUs");
+    // the model's weights were written on the default stream: order them before the table
+    WDF_CUDA_TRY(cudaDeviceSynchronize());
+    const Geo &g = c->geo;
+    const size_t rows = 2 * (size_t)c->nocc * g.ld;
+    c->ml64.ensure(sizeof(double) * rows);
+    c->ml32.ensure(sizeof(float) * rows);
+    c->mlw64.ensure(sizeof(double) * (size_t)c->nocc * g.ld);
+    launch_mlp_table(g, m->w32.as<float>(), c->U64.as<cplx<double>>() + (size_t)c->nproj * g.ld, c->tkin.as<double>(),
+                     c->eps_dev.as<double>(), c->npw_h, c->kp64.as<double>(), c->nocc, c->ml64.as<double>(), c->ml32.as<float>(),
+                     c->mlw64.as<double>(), c->st);
+    int bad = 0;
+    c->flag.ensure(sizeof(int));
+    WDF_CUDA_TRY(cudaMemsetAsync(c->flag.p, 0, sizeof(int), c->st));
+    launch_check_finite<double>(c->ml64.as<double>(), rows, c->flag.as<int>(), c->st);
+    WDF_CUDA_TRY(cudaMemcpyAsync(&bad, c->flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    if (bad) throw ApiFailure(WDF_ENAN, "the model gives non-finite preconditioner values");
+    c->opt.precond = WDF_PRECOND_LEARNED;
+    c->has_model = true;
+    return WDF_OK;
+  });
+}
+
+int wdf_train_preconditioner(wdf_ctx *const *ctx, int n, const wdf_train_opts *opt, wdf_model **out, wdf_train_stats *st) {
+  if (!out) return WDF_EINVAL;
+  *out = nullptr;
+  if (!ctx || n < 1) return WDF_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (!ctx[k] || ctx[k]->device != ctx[0]->device) {
+      set_error(WDF_EINVAL, "contexts must be non-NULL and on one GPU");
+      return WDF_EINVAL;
+    }
+  wdf_train_opts o;
+  if (opt) o = *opt;
+  else wdf_default_train_opts(&o);
+  if (o.npert < 1) return WDF_EINVAL;
+  wdf_model *m = nullptr;
+  int rc = wdf_model_create(ctx[0]->device, o.seed, &m);
+  if (rc != WDF_OK) return rc;
+  for (int k = 0; k < n && rc == WDF_OK; ++k) {
+    // perturbations: Gaussian coefficients from splitmix64(seed + k + 1), G = 0 removed, unit norm
+    const int np = ctx[k]->npw_h;
+    std::vector<double> phi(2 * (size_t)o.npert * np);
+    const uint64_t seed = o.seed + (uint64_t)k + 1;
+    for (int p = 0; p < o.npert; ++p) {
+      double nrm = 0.0;
+      for (int i = 0; i < np; ++i) {
+        double *c2 = &phi[2 * ((size_t)p * np + i)];
+        const uint64_t idx = 2 * ((uint64_t)p * np + i);
+        c2[0] = i == 0 ? 0.0 : normal_at(seed, idx);
+        c2[1] = i == 0 ? 0.0 : normal_at(seed, idx + 1);
+        nrm += 2.0 * (c2[0] * c2[0] + c2[1] * c2[1]);
+      }
+      const double s = 1.0 / std::sqrt(nrm);
+      for (int i = 0; i < 2 * np; ++i) phi[2 * (size_t)p * np + i] *= s;
+    }
+    rc = wdf_model_add_solves(m, ctx[k], o.npert, phi.data(), WDF_MEM_HOST, nullptr);
+    if (rc == WDF_ENOCONV) rc = WDF_OK;  // samples of unconverged solves are still usable
+  }
+  if (rc == WDF_OK) rc = wdf_model_train(m, &o, st);
+  if (rc != WDF_OK) {
+    wdf_model_free(m);
+    return rc;
+  }
+  *out = m;
+  return WDF_OK;
+}
 
 }  // extern "C"

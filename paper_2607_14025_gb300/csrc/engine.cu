@@ -56,6 +56,7 @@ template <> struct Prec<double> {
   static const double *vloc(wdf_ctx *c) { return c->vloc64.as<double>(); }
   static const cplx<double> *U(wdf_ctx *c) { return c->U64.as<cplx<double>>(); }
   static const double *kp(wdf_ctx *c) { return c->kp64.as<double>(); }
+  static const double *ml(wdf_ctx *c) { return c->ml64.as<double>(); }
   static wdf_ctx::Cg &cg(wdf_ctx *c) { return c->cg64; }
 };
 template <> struct Prec<float> {
@@ -63,6 +64,7 @@ template <> struct Prec<float> {
   static const float *vloc(wdf_ctx *c) { return c->vloc32.as<float>(); }
   static const cplx<float> *U(wdf_ctx *c) { return c->U32.as<cplx<float>>(); }
   static const float *kp(wdf_ctx *c) { return c->kp32.as<float>(); }
+  static const float *ml(wdf_ctx *c) { return c->ml32.as<float>(); }
   static wdf_ctx::Cg &cg(wdf_ctx *c) { return c->cg32; }
 };
 template <> struct Prec<df64> {
@@ -195,6 +197,22 @@ static int apply_operator_cg(wdf_ctx *c, cplx<T> *X, cplx<T> *Y, int n, const do
   launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, n, ea, c->st);
   const int M = c->nproj + c->nocc;
   w.S.ensure(sizeof(double) * (size_t)M * n);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->tc_on) {  // tensor-core (3xTF32) projections
+      size_t cap = 0;
+      const size_t need = gram_tc_work_doubles(g, M, n);
+      c->gramw.ensure(std::max<size_t>(need, 1) * sizeof(double));
+      cap = c->gramw.cap / sizeof(double);
+      launch_gram_tc(g, reinterpret_cast<const float *>(X), n, c->tc_uwh(), c->tc_uwl(), M, w.S.as<double>(), c->gramw.as<double>(),
+                     cap, c->tcerr.as<int>(), c->st);
+      const int kp = tc_rows(M);
+      c->tcC.ensure(sizeof(float) * 2 * (size_t)n * kp);
+      float *chi = c->tcC.as<float>(), *clo = chi + (size_t)n * kp;
+      launch_lincomb_tc(g, reinterpret_cast<float *>(Y), n, w.S.as<double>(), n, c->lrd.as<double>(), M, chi, clo, c->tc_uth(),
+                        c->tc_utl(), 1.0f, dotpart ? reinterpret_cast<const float *>(X) : nullptr, dotpart, c->tcerr.as<int>(), c->st);
+      return dotpart ? lincomb_dot_chunks(g) : 0;
+    }
+  }
   gram<T>(c, Prec<T>::U(c), M, X, n, w.S.as<double>(), n);
   if (launch_lincomb_dot<T>(g, Y, n, Prec<T>::U(c), M, w.S.as<double>(), n, c->lrd.as<double>(), 1.0, X, dotpart, c->st))
     return lincomb_dot_chunks(g);
@@ -237,6 +255,19 @@ static void cg_solve(wdf_ctx *c, const cplx<T> *b, cplx<T> *x, int n, int maxite
   cplx<T> *r = w.r.as<cplx<T>>(), *z = w.z.as<cplx<T>>(), *p = w.p.as<cplx<T>>(), *Ap = w.Ap.as<cplx<T>>();
   cudaStream_t st = c->st;
   const T *K = c->opt.precond == WDF_PRECOND_TPA ? Prec<T>::kp(c) : nullptr;
+  if (c->opt.precond == WDF_PRECOND_LEARNED) {
+    // rows of the [learned; TPA] table per solve; the row index moves to TPA on a stall
+    K = Prec<T>::ml(c);
+    w.part3.ensure(sizeof(double) * (size_t)n * nch);
+    s.krow = c->krow.as<int>();
+    s.vidx = s.krow;
+    s.vorig = c->vidx_dev.as<int>();
+    s.nocc = c->nocc;
+    s.rr_ref = c->rr_ref.as<double>();
+    s.it_ref = c->it_ref.as<int>();
+    s.part3 = w.part3.as<double>();
+    s.nfb = c->nfb.as<int>();
+  }
 
   WDF_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
   WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
@@ -294,8 +325,37 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
   nrm = c->dv_small.as<double>();
   dots<double>(c, b, b, n, nrm);
   const std::vector<double> bb = to_host(c, nrm, n);
-  WDF_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
-  WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
+  const bool learned = c->opt.precond == WDF_PRECOND_LEARNED;
+  if (learned) {
+    if (!c->has_model) throw ApiFailure(WDF_EINVAL, "WDF_PRECOND_LEARNED without a model (wdf_set_model)");
+    c->krow.ensure(sizeof(int) * n);
+    c->rr_ref.ensure(sizeof(double) * n);
+    c->it_ref.ensure(sizeof(int) * n);
+    c->nfb.ensure(sizeof(int));
+    WDF_CUDA_TRY(cudaMemcpyAsync(c->krow.p, c->vidx_dev.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    WDF_CUDA_TRY(cudaMemsetAsync(c->nfb.p, 0, sizeof(int), st));
+  }
+  // r = b - A x; A x in FP64, or in double-float (FP64 vectors converted in and out)
+  auto residual = [&]() {
+    if (c->opt.precision == WDF_MIXED_DF) {
+      c->dfa.ensure(vb);
+      c->dfb.ensure(vb);
+      to_df(c, c->dfa.as<cplx<df64>>(), x, n);
+      apply_operator<df64>(c, c->dfa.as<cplx<df64>>(), c->dfb.as<cplx<df64>>(), n, c->shift.as<double>(), true);
+      from_df(c, Ax, c->dfb.as<cplx<df64>>(), n);
+    } else {
+      apply_operator<double>(c, x, Ax, n, c->shift.as<double>(), true);
+    }
+    WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
+    launch_axpby<double>(g, r, Ax, n, -1.0, 1.0, st);
+  };
+  if (learned && c->opt.warm_start) {  // x0 = o1 K b from the model, then its residual
+    launch_first_iterate(g, x, b, c->mlw64.as<double>(), c->vidx_dev.as<int>(), n, st);
+    residual();
+  } else {
+    WDF_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
+    WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
+  }
   const double tol = c->opt.cg_tol;
   const int maxref = mixed ? 12 : 6;
   std::vector<int> iters_total(n, 0), it;
@@ -359,20 +419,20 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
       launch_axpby<double>(g, x, d, n, 1.0, 1.0, st);
     }
     for (int s = 0; s < n; ++s) iters_total[s] += it[s];
-    // r = b - A x; A x in FP64, or in double-float (FP64 vectors converted in and out)
-    if (c->opt.precision == WDF_MIXED_DF) {
-      c->dfa.ensure(vb);
-      c->dfb.ensure(vb);
-      to_df(c, c->dfa.as<cplx<df64>>(), x, n);
-      apply_operator<df64>(c, c->dfa.as<cplx<df64>>(), c->dfb.as<cplx<df64>>(), n, c->shift.as<double>(), true);
-      from_df(c, Ax, c->dfb.as<cplx<df64>>(), n);
-    } else {
-      apply_operator<double>(c, x, Ax, n, c->shift.as<double>(), true);
-    }
-    WDF_CUDA_TRY(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
-    launch_axpby<double>(g, r, Ax, n, -1.0, 1.0, st);
+    residual();
+  }
+  if (c->tc_on) {
+    int terr = 0;
+    WDF_CUDA_TRY(cudaMemcpyAsync(&terr, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WDF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (terr) throw ApiFailure(WDF_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
   }
   ss.converged = conv;
+  ss.fallbacks = 0;
+  if (learned) {
+    WDF_CUDA_TRY(cudaMemcpyAsync(&ss.fallbacks, c->nfb.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WDF_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   ss.iters = 0;
   ss.iters_max = 0;
   ss.max_res = 0.0;
@@ -476,6 +536,8 @@ static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, cplx<do
     std::vector<int> vidx(ns);
     for (int s = 0; s < ns; ++s) vidx[s] = (s / 2) % nocc;
     sternheimer_solve(c, b, x, vidx.data(), ns, sc);
+    if (c->collect) launch_mlp_accum(g, b, x, ns, nocc, c->kp64.as<double>(), c->mlsums.as<double>(), st);
+    ss.fallbacks += sc.fallbacks;
     ss.iters += sc.iters;
     ss.iters_max = std::max(ss.iters_max, sc.iters_max);
     ss.refinements = std::max(ss.refinements, sc.refinements);
@@ -569,6 +631,32 @@ static int orthonormalise(wdf_ctx *c, cplx<double> *V, int nb, int nnew, double 
   for (int pass = 0; pass < 2 && nb > 0; ++pass) {
     gram<double>(c, V, nb, Nw, nnew, C, nnew);
     launch_lincomb<double>(g, Nw, nnew, V, nb, C, nnew, neg, 1.0, st);
+  }
+  // within the block: CholeskyQR2 (Gram matrix, Cholesky, N <- N L^-T, twice) when the block is
+  // well conditioned; near-dependent blocks take the vector-by-vector path below, which drops
+  if (nnew > 1 && nnew <= kCholMax) {
+    const size_t nn = (size_t)nnew * nnew;
+    c->chol.ensure(sizeof(double) * 2 * nn + sizeof(int));
+    c->rwork.ensure(sizeof(cplx<double>) * (size_t)nnew * g.ld);
+    double *Gm = c->chol.as<double>(), *Cf = Gm + nn;
+    int *ok = reinterpret_cast<int *>(Cf + nn);
+    cplx<double> *tmp = c->rwork.as<cplx<double>>();
+    int good = 1;
+    for (int pass = 0; pass < 2 && good; ++pass) {
+      gram<double>(c, Nw, nnew, Nw, nnew, Gm, nnew);
+      // CholeskyQR squares the condition number: accept pivots above 1e-12 of the largest
+      launch_chol_inv(Gm, nnew, Cf, pass == 0 ? 1e-12 : 0.25, ok, st);
+      WDF_CUDA_TRY(cudaMemcpyAsync(&good, ok, sizeof(int), cudaMemcpyDeviceToHost, st));
+      WDF_CUDA_TRY(cudaStreamSynchronize(st));
+      if (!good) break;
+      launch_lincomb<double>(g, tmp, nnew, Nw, nnew, Cf, nnew, nullptr, 0.0, st);
+      // the lincomb writes elements [0, nint) of each row; the padding of Nw stays as it was
+      const size_t row = sizeof(cplx<double>) * (size_t)g.ld;
+      WDF_CUDA_TRY(cudaMemcpy2DAsync(Nw, row, tmp, row, sizeof(cplx<double>) * (size_t)g.nint, nnew, cudaMemcpyDeviceToDevice, st));
+    }
+    if (good) return nnew;
+    // fall back: the block may have lost orthogonality in the first pass; the sequential path
+    // below re-orthonormalises from the current vectors
   }
   int kept = 0;
   for (int i = 0; i < nnew; ++i) {
@@ -770,6 +858,16 @@ void finish_setup(wdf_ctx *c) {
   // FP32 copy of the projectors and orbitals
   c->U32.ensure(sizeof(cplx<float>) * (size_t)M * g.ld);
   launch_convert<double, float>(g, (float *)c->U32.p, (const double *)c->U64.p, 2 * (size_t)M * g.ld, st);
+  // tensor-core copies of U for the FP32 projections (at most 256 rows fit one MMA)
+  c->tc_on = tc_enabled() && M >= 1 && M <= 256;
+  if (c->tc_on) {
+    const int kp = tc_rows(M);
+    c->tcU.ensure(sizeof(float) * 2 * (size_t)M * 2 * g.ld);
+    c->tcUt.ensure(sizeof(float) * 2 * (size_t)2 * g.ld * kp);
+    c->tcerr.ensure(sizeof(int));
+    WDF_CUDA_TRY(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), st));
+    launch_tc_prep_u(g, c->U32.as<float2>(), M, c->tc_uwh(), c->tc_uwl(), c->tc_uth(), c->tc_utl(), st);
+  }
   if (c->opt.precision == WDF_MIXED_DF) {  // double-float copies for residuals and density
     c->Udf.ensure(sizeof(cplx<df64>) * (size_t)M * g.ld);
     to_df(c, c->Udf.as<cplx<df64>>(), c->U64.as<cplx<double>>(), M);

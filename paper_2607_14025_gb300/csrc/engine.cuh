@@ -75,14 +75,29 @@ struct wdf_ctx {
 
   // workspaces (grow-only)
   struct Cg {
-    wdf::DBuf r, z, p, Ap, x, cb, S, part1, part2, dbl, ints;
+    wdf::DBuf r, z, p, Ap, x, cb, S, part1, part2, part3, dbl, ints;
   } cg64, cg32, cgdf;
+  // learned preconditioner (wdf_set_model): [2 nocc][ld] tables (learned rows, then TPA rows),
+  // first-iterate gains [nocc][ld]; per-solve row index, stall-check state and fallback counter
+  wdf::DBuf ml64, ml32, mlw64, krow, rr_ref, it_ref, nfb;
+  // tensor-core projections of the FP32 CG: weighted U (hi, lo) [M][2 ld], U^T (hi, lo)
+  // [2 ld][kp], coefficient staging, wait-expiry flag
+  wdf::DBuf tcU, tcUt, tcC, tcerr;
+  bool tc_on = false;
+  float *tc_uwh() const { return tcU.as<float>(); }
+  float *tc_uwl() const { return tcU.as<float>() + (size_t)(nproj + nocc) * 2 * geo.ld; }
+  float *tc_uth() const { return tcUt.as<float>(); }
+  float *tc_utl() const { return tcUt.as<float>() + (size_t)2 * geo.ld * wdf::tc_rows(nproj + nocc); }
+  bool has_model = false;
+  // training-sample collection (wdf_model_add_solves): sums [3][nocc][ld] over converged solves
+  wdf::DBuf mlsums, mlwraw;
+  bool collect = false;
   wdf::DBuf rb, rx, rr, rAx, rwork;        // refinement: b, x, r, A x (FP64), FP32 staging
   wdf::DBuf shift, vidx_dev, thr;          // per-solve shift, orbital index, thresholds
   wdf::DBuf gramw;                         // split partial sums of Gram products
   wdf::DBuf xpert, dvgrid, accgrid, cb2, outi, drhoi, ext_in, ext_out, ext_out2;
   wdf::DBuf dv_V, dv_W, dv_X, dv_AX, dv_R, dv_H, dv_Y, dv_theta, dv_jac, dv_jint, dv_small, dv_neg;
-  wdf::DBuf zeros, flag, guess, chi_out, chi_drho;
+  wdf::DBuf zeros, flag, guess, chi_out, chi_drho, chol;
   wdf::DBuf dfa, dfb, xpdf, dvgriddf, accgriddf, cb2df, drdf, oudf;  // double-float work
 
   // kernel timing (wdf_profile_kernel)
@@ -102,6 +117,7 @@ struct SolveStats {
   int refinements = 0;
   double max_res = 0;
   bool converged = true;
+  int fallbacks = 0;  // learned preconditioner: solves that restarted with TPA
 };
 
 // Solve (H - eps_v + alpha P) x = b for n right-hand sides in internal FP64 layout.
@@ -129,7 +145,25 @@ struct DavResult {
 DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nwant, int nkeep, int nbmax,
                    int maxiter, double tol, bool zero_g0);
 
+// x[s] = w[v_s] b[s] elementwise (first iterate of a solve from a per-(v, e) gain table)
+void launch_first_iterate(const Geo &g, cplx<double> *x, const cplx<double> *b, const double *w, const int *vidx, int n,
+                          cudaStream_t st);
+
 void ground_state(wdf_ctx *c);     // fills U64 psi rows and c->eps
 void finish_setup(wdf_ctx *c);     // derived tables once psi and eps are known
 
 }  // namespace wdf
+
+// A learned-preconditioner model on one GPU (include/wdf.h).
+struct wdf_model {
+  int device = 0;
+  std::string err;
+  wdf::DBuf w64, w32;          // weights: FP64 master copy (kMlpFloats), FP32 copy for the kernels
+  wdf::DBuf m, v;              // Adam moments (kMlpParams doubles each)
+  wdf::DBuf grad, part;        // gradient + loss (kMlpParams + 1), per-block partials
+  wdf::DBuf feat, tgt, wt;     // samples: [cap][4], [cap][2], [cap][2] floats
+  wdf::DBuf pin, pout;         // staging of wdf_model_predict
+  long long n = 0, cap = 0;    // samples held, capacity
+  int t = 0;                   // Adam steps taken
+  bool fresh = true;           // weights from wdf_model_create: first training sets mu, sd, b3
+};

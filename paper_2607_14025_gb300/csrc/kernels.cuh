@@ -92,14 +92,25 @@ struct CgState {
   int *active;                           // 1 while the solve iterates
   int *iters;                            // iterations done
   int *nactive;                          // [1] count of active solves
-  int *vidx;                             // occupied orbital of each solve
+  int *vidx;                             // preconditioner row of each solve (its orbital for TPA)
+  // learned preconditioner only (krow null otherwise): rows [0, nocc) of the table are learned,
+  // rows [nocc, 2 nocc) TPA; a solve whose <r,r> falls by less than 19% over 5 iterations (||r||
+  // by less than 10%) moves to its TPA row and restarts with beta = 0
+  int *krow = nullptr;                   // = vidx (the same array) when the table is learned
+  const int *vorig = nullptr;            // orbital of each solve
+  int nocc = 0;
+  double *rr_ref = nullptr;              // <r,r> at the last stall check
+  int *it_ref = nullptr;                 // iteration of the last stall check
+  double *part3 = nullptr;               // partials of <r, K_TPA r> [n * nchunk]
+  int *nfb = nullptr;                    // [1] solves moved to TPA
 };
 
 // z = K r (TPA per orbital), p = z, and partials for <r,z>, <r,r>
 template <typename T>
 void launch_cg_start(const Geo &g, const cplx<T> *r, cplx<T> *z, cplx<T> *p, const T *kprec, const CgState &s, int n,
                      int nchunk, cudaStream_t st);
-// alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = K r; partials <r,z>, <r,r>
+// alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = K r; partials <r,z>, <r,r> (and, for the
+// learned table, <r, K_TPA r> of the solves still on a learned row)
 template <typename T>
 void launch_cg_update(const Geo &g, cplx<T> *x, cplx<T> *r, cplx<T> *z, const cplx<T> *p, const cplx<T> *Ap,
                       const T *kprec, const CgState &s, int n, int nchunk, cudaStream_t st);
@@ -129,6 +140,50 @@ template <typename T> void launch_tpa_table(const Geo &g, T *K, const double *tk
 void launch_kinetic(const Geo &g, const cplx<double> *X, int n, double *tkin, cudaStream_t st);
 // check for non-finite values; sets *flag = 1 if any
 template <typename T> void launch_check_finite(const T *x, size_t count, int *flag, cudaStream_t st);
+
+// Cholesky of an n x n SPD matrix and inverse of its factor in one block (n <= 160): writes the
+// coefficients C = L^-T for launch_lincomb and *ok = 0 when a pivot is below tol * max diagonal
+void launch_chol_inv(const double *G, int n, double *C, double tol, int *ok, cudaStream_t st);
+size_t chol_inv_smem(int n);
+void set_chol_inv_limits(int nmax);
+constexpr int kCholMax = 160;  // n^2 + n doubles of shared memory (<= 227 KB)
+
+// learned preconditioner (mlp.cu): weights W[kMlpFloats] = W1[4][64], b1, W2[64][64], b2, W3[64][2],
+// b3 (kMlpParams trained values), mu[4], sd[4]; samples feat[n][4], tgt[n][2], wt[n][2]
+constexpr int kMlpParams = 4610;
+constexpr int kMlpFloats = 4618;
+size_t mlp_grad_smem();
+void set_mlp_limits();
+int mlp_grad_blocks(long long n);
+// out[0 .. kMlpParams) = gradient, out[kMlpParams] = loss; part: mlp_grad_blocks(n) * (kMlpParams + 1)
+void launch_mlp_grad(const float *W, const float *feat, const float *tgt, const float *wt, long long n, double *part, double *out,
+                     cudaStream_t st);
+void launch_mlp_adam(double *w64, float *w32, const double *grad, double *m, double *v, int t, double lr, cudaStream_t st);
+// m64/m32 [2 nocc][ld]: rows v = s(v,e) K(v,e), rows nocc + v = K(v,e); w64 [nocc][ld] = o1 K
+void launch_mlp_table(const Geo &g, const float *W, const cplx<double> *psi, const double *tkin, const double *eps, int npw_h,
+                      const double *ktpa, int nocc, double *m64, float *m32, double *w64, cudaStream_t st);
+void launch_mlp_predict(const float *W, const float *feat, long long n, float *out, cudaStream_t st);
+// sums [3][nocc][ld] += (|x|^2, |K b|^2, Re(conj(K b) x)) over the solves of a chi0bar block
+void launch_mlp_accum(const Geo &g, const cplx<double> *b, const cplx<double> *x, int ns, int nocc, const double *ktpa, double *sums,
+                      cudaStream_t st);
+// nocc * npw_h samples (v-major, external order) from the sums; wraw: 2 n doubles, wsum: 2
+void launch_mlp_samples(const Geo &g, const int *emap, int npw_h, int nocc, const double *sums, const cplx<double> *psi,
+                        const double *tkin, const double *eps, float *feat, float *tgt, float *wt, double *wraw, double *wsum,
+                        cudaStream_t st);
+
+// tensor-core (tcgen05 kind::tf32, three-term split) projections of the FP32 CG (tc_gemm.cu);
+// on when WDF_TC is set in the environment (WDF_NO_TC wins)
+bool tc_enabled();
+int tc_rows(int na);  // rows of U rounded up to 32 (the MMA N of the projections, <= 256)
+void set_tc_limits();
+void launch_tc_prep_u(const Geo &g, const float2 *U, int na, float *uwh, float *uwl, float *uth, float *utl, cudaStream_t st);
+size_t gram_tc_work_doubles(const Geo &g, int na, int nb);
+// out[j][s] (ldo = nb) = sum_e w_e Re(conj(U_j) X_s) for j < na, s < nb
+void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, const float *uwl, int na, double *out, double *work,
+                    size_t work_cap, int *err, cudaStream_t st);
+// Y_s = c0 Y_s + sum_j U_j S[j][s] d_j, partial <P_s, Y_s> per 128-element tile when part != null
+void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc, const double *d, int na, float *chi, float *clo,
+                       const float *uth, const float *utl, float c0, const float *P, double *part, int *err, cudaStream_t st);
 
 // symmetric eigensolver (cyclic Jacobi, parallel ordering) of an n x n matrix A (ld = n), FP64.
 // On exit w holds eigenvalues ascending and V[i * n + k] the i-th component of eigenvector k.

@@ -510,11 +510,14 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo g, cplx<T> *__restrict__ 
                                                   const cplx<T> *__restrict__ p, const cplx<T> *__restrict__ Ap,
                                                   const T *__restrict__ kprec, CgState s, int nchunk) {
   const int i = blockIdx.x, c = blockIdx.y;
-  double vrz = 0.0, vrr = 0.0;
+  double vrz = 0.0, vrr = 0.0, vr3 = 0.0;
+  // learned table: also <r, K_TPA r> while the solve is on its learned row (for a restart)
+  const bool fb = s.krow && s.krow[i] < s.nocc;
   if (s.active[i]) {
     const int e0 = c * DCHUNK, e1 = min(g.nint, e0 + DCHUNK);
     const size_t o = (size_t)i * g.ld;
     const T *K = kprec ? kprec + (size_t)s.vidx[i] * g.ld : nullptr;
+    const T *K3 = fb ? kprec + (size_t)(s.vorig[i] + s.nocc) * g.ld : nullptr;
     const T al = (T)(s.rz[i] / s.pap[i]);
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const cplx<T> pv = p[o + e], av = Ap[o + e];
@@ -531,13 +534,16 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo g, cplx<T> *__restrict__ 
       const double w = wgt(e, g.len0);
       vrz += w * dre<T>(rv, zv);
       vrr += w * dre<T>(rv, rv);
+      if (K3) vr3 += w * (double)K3[e] * dre<T>(rv, rv);
     }
   }
   vrz = block_sum(vrz);
   vrr = block_sum(vrr);
+  if (fb) vr3 = block_sum(vr3);
   if (threadIdx.x == 0) {
     s.part1[(size_t)i * nchunk + c] = vrz;
     s.part2[(size_t)i * nchunk + c] = vrr;
+    if (fb) s.part3[(size_t)i * nchunk + c] = vr3;
   }
 }
 
@@ -587,6 +593,10 @@ __global__ void k_cg_scalars(CgState s, int n, int nchunk, int which, int maxite
     const int act = (b > s.thr[i]) && (b > 0.0) && (s.iters[i] < maxiter);
     s.active[i] = act;
     if (act) atomicAdd(s.nactive, 1);
+    if (s.krow) {
+      s.rr_ref[i] = b;
+      s.it_ref[i] = s.iters[i];
+    }
     return;
   }
   if (!s.active[i]) return;
@@ -597,8 +607,20 @@ __global__ void k_cg_scalars(CgState s, int n, int nchunk, int which, int maxite
   s.rz_new[i] = beta;
   if (b <= s.thr[i] || s.iters[i] >= maxiter || !(b == b)) {
     s.active[i] = 0;
-  } else {
-    atomicAdd(s.nactive, 1);
+    return;
+  }
+  atomicAdd(s.nactive, 1);
+  if (s.krow && s.krow[i] < s.nocc && s.iters[i] - s.it_ref[i] >= 5) {
+    if (b > 0.81 * s.rr_ref[i]) {  // stalled on the learned row: TPA from the current iterate
+      double c3 = 0.0;
+      for (int c = 0; c < nchunk; ++c) c3 += s.part3[(size_t)i * nchunk + c];
+      s.krow[i] = s.vorig[i] + s.nocc;
+      s.rz[i] = c3;
+      s.rz_new[i] = 0.0;  // beta = 0: p = K_TPA r
+      atomicAdd(s.nfb, 1);
+    }
+    s.rr_ref[i] = b;
+    s.it_ref[i] = s.iters[i];
   }
 }
 
@@ -874,6 +896,75 @@ __global__ void k_jac_sort(const double *__restrict__ A, const double *__restric
     w[rank] = di;
     for (int k = 0; k < n; ++k) V[(size_t)k * n + rank] = Vw[(size_t)k * m + i];
   }
+}
+
+// Cholesky factorisation G = L L^T of an n x n symmetric positive definite matrix (FP64, one
+// block, in shared memory) followed by the inverse of L; writes C[j * n + s] = (L^-1)[s][j] (so
+// that Y_s = sum_j X_j C[j][s] is X L^-T) and sets *ok = 0 if a pivot falls below tol times the
+// largest diagonal entry (near-dependent columns). Shared memory: L in the lower triangle, the
+// strictly lower part of L^-1 transposed into the upper triangle, and the diagonal of L^-1 apart.
+__global__ void k_chol_inv(const double *__restrict__ G, int n, double *__restrict__ C, double tol, int *ok) {
+  extern __shared__ double sm[];
+  double *A = sm;          // n x n
+  double *dli = sm + n * n;  // diagonal of L^-1
+  __shared__ double dmax;
+  __shared__ int good;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    A[t] = (j <= i) ? 0.5 * (G[(size_t)i * n + j] + G[(size_t)j * n + i]) : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    good = 1;
+    dmax = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < n; ++i) dmax = fmax(dmax, A[i * n + i]);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {  // right-looking: column j, then the trailing lower triangle
+    if (threadIdx.x == 0) {
+      const double d = A[j * n + j];
+      if (!(d > tol * dmax)) good = 0;
+      A[j * n + j] = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    const double piv = A[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + j] /= piv;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = j + 1 + t / m, k = j + 1 + t % m;
+      if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
+    }
+    __syncthreads();
+  }
+  // forward substitution L Li = I; thread c builds column c of Li: Li[c][c] -> dli[c],
+  // Li[i][c] (i > c) -> A[c * n + i]
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    dli[c] = 1.0 / A[c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+      double v = -A[i * n + c] * dli[c];
+      for (int k = c + 1; k < i; ++k) v -= A[i * n + k] * A[c * n + k];
+      A[c * n + i] = v / A[i * n + i];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int j = t / n, s2 = t % n;  // C[j][s] = Li[s][j]
+    C[t] = (s2 < j) ? 0.0 : (s2 == j ? dli[j] : A[j * n + s2]);
+  }
+  if (threadIdx.x == 0) *ok = good;
+}
+
+size_t chol_inv_smem(int n) { return sizeof(double) * ((size_t)n * n + n); }
+
+void launch_chol_inv(const double *G, int n, double *C, double tol, int *ok, cudaStream_t st) {
+  launch("chol_inv", 0, k_chol_inv, dim3(1), dim3(256), chol_inv_smem(n), st, G, n, C, tol, ok);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+void set_chol_inv_limits(int nmax) {
+  WDF_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_inv_smem(nmax)));
 }
 
 size_t jacobi_work_doubles(int n) {

@@ -507,6 +507,14 @@ __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict
   }
 }
 
+// sizes with the register kernels: N = 8 R2, R2 in {3, 4, 5, 8}
+#define WDF_REG_SIZES(X) X(24) X(32) X(40) X(64)
+
+static bool reg_plane_enabled() {
+  static const bool on = std::getenv("WDF_NO_REG_PLANE") == nullptr;
+  return on;
+}
+
 template <int N> size_t reg_smem(const Geo &g) {
   return sizeof(float2) * ((size_t)N + (size_t)N * (N + 1)) + sizeof(float) * (size_t)N * (N + 1) + sizeof(int) * (size_t)g.nxact;
 }
@@ -516,13 +524,6 @@ template <int N> static void launch_reg(const FftCtx<float> &f, int nblk, const 
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
-// sizes with the register kernel: N = 8 R2, R2 in {3, 4, 5, 8}
-#define WDF_REG_SIZES(X) X(24) X(32) X(40) X(64)
-
-static bool reg_plane_enabled() {
-  static const bool on = std::getenv("WDF_NO_REG_PLANE") == nullptr;
-  return on;
-}
 
 void set_plane_reg_limits(const Geo &g) {
   switch (g.n1) {

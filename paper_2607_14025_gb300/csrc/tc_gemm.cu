@@ -1,0 +1,380 @@
+// Tensor-core (tcgen05, kind::tf32) forms of the two dense products of the FP32 inner CG:
+//   gram:    S[j][s] = sum_e w_e Re(conj(U_j[e]) X_s[e])       (projections on [beta; psi])
+//   lincomb: Y_s = c0 Y_s + sum_j U_j S[j][s] d_j               (KB term and alpha P shift)
+// Complex vectors are read as real rows of 2 N_int values, so both are real GEMMs with K-major
+// operands. FP32 accuracy from TF32 units by the three-term split a b ~ a_h b_h + a_h b_l + a_l b_h
+// with a_h the upper 19 bits of a and a_l = a - a_h (the dropped a_l b_l is ~2^-22 |a b|).
+// Operand tiles are staged through registers (the low parts and the zero padding are made on
+// the way) into 128-byte-swizzled shared memory, two stages deep; one thread issues the MMAs and
+// commits them to the stage's mbarrier; accumulators sit in TMEM and the epilogue reads them with
+// tcgen05.ld. Every mbarrier wait is bounded: on expiry the kernel raises a flag, waits (bounded)
+// for what it issued, frees its TMEM and returns.
+#include <cstdlib>
+
+#include "engine.cuh"
+#include "tc.cuh"
+
+namespace wdf {
+
+namespace {
+
+constexpr int TM = 128;              // MMA M: solves per tile
+constexpr int TK = 32;               // K values per stage (one 128-byte row)
+constexpr int XB = TM * 128;         // bytes of a 128-row operand tile
+constexpr long kWaitLimit = 1L << 26;  // polls of an mbarrier before giving up
+
+__device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
+  return (unsigned char *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+// stage a 16-byte piece (hi and lo) into swizzled tiles
+__device__ __forceinline__ void put(unsigned char *hi, unsigned char *lo, int row, int q, float4 v) {
+  const int o = tc::swz_off(row, q);
+  *reinterpret_cast<float4 *>(hi + o) = v;
+  *reinterpret_cast<float4 *>(lo + o) = make_float4(tc::tf32_low(v.x), tc::tf32_low(v.y), tc::tf32_low(v.z), tc::tf32_low(v.w));
+}
+
+// element f .. f+3 of a row, zero at and beyond kf
+__device__ __forceinline__ float4 load_masked(const float *row, int f, int kf) {
+  if (f + 3 < kf) return *reinterpret_cast<const float4 *>(row + f);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (f < kf) v.x = row[f];
+  if (f + 1 < kf) v.y = row[f + 1];
+  if (f + 2 < kf) v.z = row[f + 2];
+  return v;
+}
+
+// S (+ split partials) = U_w X^T; grid (solve tiles, splits), 256 threads
+__global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restrict__ X, int nb, const float *__restrict__ Uhi,
+                                                    const float *__restrict__ Ulo, int na, int nu, double *__restrict__ out, int ldo,
+                                                    int ch_per_split, size_t split_stride, int *__restrict__ err) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = align1024(smraw);
+  const int UB = nu * 128, SB = 2 * XB + 2 * UB;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * SB);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + 2 * SB + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s0 = blockIdx.x * TM;
+  const int kf = 2 * g.nint, ldf = 2 * g.ld;
+  const int nch = (kf + TK - 1) / TK;
+  const int c0 = blockIdx.y * ch_per_split, c1 = min(nch, c0 + ch_per_split);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(slot, 256);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  const uint32_t idesc = tc::idesc_tf32(TM, nu);
+  int issued = 0;
+  bool ok = true;
+  for (int c = c0; c < c1; ++c) {
+    const int i = c - c0, st = i & 1;
+    unsigned char *S = sm + st * SB;
+    if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
+    if (!ok) break;
+    const int f0 = c * TK;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {  // X: 128 rows x 8 pieces
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s0 + row < nb) v = load_masked(X + (size_t)(s0 + row) * ldf, f0 + 4 * q, kf);
+      put(S, S + XB, row, q, v);
+    }
+    for (int t = tid; t < nu * 8; t += 256) {  // U (weighted, split at setup): nu rows x 8 pieces
+      const int row = t >> 3, q = t & 7;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+      if (row < na) {
+        h = *reinterpret_cast<const float4 *>(Uhi + (size_t)row * ldf + f0 + 4 * q);
+        l = *reinterpret_cast<const float4 *>(Ulo + (size_t)row * ldf + f0 + 4 * q);
+      }
+      const int o = tc::swz_off(row, q);
+      *reinterpret_cast<float4 *>(S + 2 * XB + o) = h;
+      *reinterpret_cast<float4 *>(S + 2 * XB + UB + o) = l;
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t base = tc::smem_u32(S);
+#pragma unroll
+      for (int term = 0; term < 3; ++term) {
+        const uint32_t a = base + (term == 2 ? XB : 0), b = base + 2 * XB + (term == 1 ? UB : 0);
+#pragma unroll
+        for (int ks = 0; ks < TK / 8; ++ks)
+          tc::mma_tf32(tmem, tc::desc_sw128(a + 32 * ks), tc::desc_sw128(b + 32 * ks), idesc, (i | term | ks) ? 1u : 0u);
+      }
+      tc::mma_commit(&bar[st]);
+    }
+    ++issued;
+  }
+  // the last commit covers every MMA issued
+  bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
+  done = __syncthreads_and(done) && ok && issued == c1 - c0;
+  if (done) {
+    tc::fence_after_sync();
+    const int qd = warp & 3, h = warp >> 2, row = 32 * qd + lane, s = s0 + row;
+    double *o = out + (size_t)blockIdx.y * split_stride;
+    const int half = nu / 2;
+    for (int cg = 0; cg < half; cg += 16) {
+      const int col = h * half + cg;
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)col, v);
+      if (s < nb)
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (col + k < na) o[(size_t)(col + k) * ldo + s] = (double)v[k];
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+__global__ void k_tc_sum_splits(const double *__restrict__ work, int nsplit, size_t stride, double *__restrict__ out, int na, int nb,
+                                int ldo) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)na * nb) return;
+  const int j = (int)(t / nb), s = (int)(t % nb);
+  double a = 0.0;
+  for (int k = 0; k < nsplit; ++k) a += work[k * stride + (size_t)j * ldo + s];
+  out[(size_t)j * ldo + s] = a;
+}
+
+// Cd[s][j] = S[j][s] d_j (j < na, else 0), hi and lo parts, through a 32 x 32 shared tile
+__global__ void k_tc_coef(const double *__restrict__ S, int ldc, const double *__restrict__ d, int na, int nb, int kp,
+                          float *__restrict__ hi, float *__restrict__ lo) {
+  __shared__ float tile[32][33];
+  const int j0 = blockIdx.y * 32, s0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, s = s0 + threadIdx.x;
+    float v = 0.f;
+    if (j < na && s < nb) v = (float)(S[(size_t)j * ldc + s] * (d ? d[j] : 1.0));
+    tile[r][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int s = s0 + r, j = j0 + threadIdx.x;
+    if (s < nb && j < kp) {
+      const float v = tile[threadIdx.x][r];
+      hi[(size_t)s * kp + j] = v;
+      lo[(size_t)s * kp + j] = tc::tf32_low(v);
+    }
+  }
+}
+
+// Y = c0 Y + Cd Ut^T on float rows (2 N_int), partial <P_s, Y_s> per 128-element tile;
+// grid (solve tiles, 256-value tiles), 256 threads
+__global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict__ Y, int ny, const float *__restrict__ Chi,
+                                                       const float *__restrict__ Clo, int kp, const float *__restrict__ Uthi,
+                                                       const float *__restrict__ Utlo, float c0, const float *__restrict__ P,
+                                                       double *__restrict__ part, int nchunk, int *__restrict__ err) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = align1024(smraw);
+  constexpr int TN = 256, BB = TN * 128, SB = 2 * XB + 2 * BB;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * SB);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + 2 * SB + 16);
+  double *red = reinterpret_cast<double *>(sm + 2 * SB + 64);  // [2][128]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s0 = blockIdx.x * TM, f0 = blockIdx.y * TN;
+  const int kf = 2 * g.nint, ldf = 2 * g.ld;
+  const int nkc = kp / TK;
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(slot, 256);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  const uint32_t idesc = tc::idesc_tf32(TM, TN);
+  int issued = 0;
+  bool ok = true;
+  for (int i = 0; i < nkc; ++i) {
+    const int st = i & 1;
+    unsigned char *S = sm + st * SB;
+    if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
+    if (!ok) break;
+    const int k0 = i * TK;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {  // coefficients: 128 solve rows x 8 pieces (hi, lo precomputed)
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+      if (s0 + row < ny) {
+        h = *reinterpret_cast<const float4 *>(Chi + (size_t)(s0 + row) * kp + k0 + 4 * q);
+        l = *reinterpret_cast<const float4 *>(Clo + (size_t)(s0 + row) * kp + k0 + 4 * q);
+      }
+      const int o = tc::swz_off(row, q);
+      *reinterpret_cast<float4 *>(S + o) = h;
+      *reinterpret_cast<float4 *>(S + XB + o) = l;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {  // U transposed: 256 value rows x 8 pieces
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+      if (f0 + row < kf) {
+        h = *reinterpret_cast<const float4 *>(Uthi + (size_t)(f0 + row) * kp + k0 + 4 * q);
+        l = *reinterpret_cast<const float4 *>(Utlo + (size_t)(f0 + row) * kp + k0 + 4 * q);
+      }
+      const int o = tc::swz_off(row, q);
+      *reinterpret_cast<float4 *>(S + 2 * XB + o) = h;
+      *reinterpret_cast<float4 *>(S + 2 * XB + BB + o) = l;
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t base = tc::smem_u32(S);
+#pragma unroll
+      for (int term = 0; term < 3; ++term) {
+        const uint32_t a = base + (term == 2 ? XB : 0), b = base + 2 * XB + (term == 1 ? BB : 0);
+#pragma unroll
+        for (int ks = 0; ks < TK / 8; ++ks)
+          tc::mma_tf32(tmem, tc::desc_sw128(a + 32 * ks), tc::desc_sw128(b + 32 * ks), idesc, (i | term | ks) ? 1u : 0u);
+      }
+      tc::mma_commit(&bar[st]);
+    }
+    ++issued;
+  }
+  bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
+  done = __syncthreads_and(done) && ok && issued == nkc;
+  const int qd = warp & 3, h = warp >> 2, row = 32 * qd + lane, s = s0 + row;
+  double dsum = 0.0;
+  if (done) {
+    tc::fence_after_sync();
+    for (int cg = 0; cg < TN / 2; cg += 16) {
+      const int col = h * (TN / 2) + cg;
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)col, v);
+      if (s < ny) {
+        float *y = Y + (size_t)s * ldf;
+        const float *p = P ? P + (size_t)s * ldf : nullptr;
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) {
+          const int f = f0 + col + k;  // even: one complex element e = f / 2
+          if (f < kf) {
+            float yx = v[k], yy = v[k + 1];
+            if (c0 != 0.f) {
+              const float2 o = *reinterpret_cast<const float2 *>(y + f);
+              yx = fmaf(c0, o.x, yx);
+              yy = fmaf(c0, o.y, yy);
+            }
+            *reinterpret_cast<float2 *>(y + f) = make_float2(yx, yy);
+            if (p) {
+              const float2 pv = *reinterpret_cast<const float2 *>(p + f);
+              const double w = (f >> 1) < g.len0 ? 1.0 : 2.0;
+              dsum += w * ((double)pv.x * yx + (double)pv.y * yy);
+            }
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  if (part) {
+    red[h * TM + row] = dsum;
+    __syncthreads();
+    if (tid < TM && s0 + tid < ny) part[(size_t)(s0 + tid) * nchunk + blockIdx.y] = red[tid] + red[TM + tid];
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// U_w = w U (hi, lo) as [na][2 ld] and U^T (hi, lo) as [2 ld][kp], zero padded
+__global__ void k_tc_prep_u(Geo g, const float2 *__restrict__ U, int na, int kp, float *__restrict__ uwh, float *__restrict__ uwl,
+                            float *__restrict__ uth, float *__restrict__ utl) {
+  const int ldf = 2 * g.ld;
+  const size_t tot = (size_t)ldf * kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / ldf), f = (int)(t % ldf), e = f >> 1;
+    float v = 0.f;
+    if (j < na && e < g.nint) {
+      const float2 u = U[(size_t)j * g.ld + e];
+      v = (f & 1) ? u.y : u.x;
+    }
+    if (j < na) {
+      const float w = e < g.len0 ? v : 2.f * v;
+      uwh[(size_t)j * ldf + f] = w;
+      uwl[(size_t)j * ldf + f] = tc::tf32_low(w);
+    }
+    uth[(size_t)f * kp + j] = v;
+    utl[(size_t)f * kp + j] = tc::tf32_low(v);
+  }
+}
+
+size_t gram_tc_smem(int nu) { return 1024 + 2 * (size_t)(2 * XB + 2 * nu * 128) + 64; }
+size_t lincomb_tc_smem() { return 1024 + 2 * (size_t)(2 * XB + 2 * 256 * 128) + 64 + 2 * TM * sizeof(double); }
+
+}  // namespace
+
+bool tc_enabled() {
+  static const bool on = std::getenv("WDF_TC") != nullptr && std::getenv("WDF_NO_TC") == nullptr;
+  return on;
+}
+
+int tc_rows(int na) { return ((na + 31) / 32) * 32; }
+
+void set_tc_limits() {
+  WDF_CUDA_TRY(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem(256)));
+  WDF_CUDA_TRY(cudaFuncSetAttribute(k_lincomb_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lincomb_tc_smem()));
+}
+
+void launch_tc_prep_u(const Geo &g, const float2 *U, int na, float *uwh, float *uwl, float *uth, float *utl, cudaStream_t st) {
+  const int kp = tc_rows(na);
+  launch("tc_prep", 32, k_tc_prep_u, dim3(2048), dim3(256), 0, st, g, U, na, kp, uwh, uwl, uth, utl);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+size_t gram_tc_work_doubles(const Geo &g, int na, int nb) {
+  const int nch = (2 * g.nint + TK - 1) / TK;
+  const int tiles = (nb + TM - 1) / TM;
+  int nsplit = std::max(1, std::min((2 * 152 + tiles - 1) / tiles, nch / 8));
+  return nsplit > 1 ? (size_t)nsplit * na * nb : 0;
+}
+
+void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, const float *uwl, int na, double *out, double *work,
+                    size_t work_cap, int *err, cudaStream_t st) {
+  if (nb <= 0 || na <= 0) return;
+  const int nu = tc_rows(na);
+  const int nch = (2 * g.nint + TK - 1) / TK;
+  const int tiles = (nb + TM - 1) / TM;
+  int nsplit = std::max(1, std::min((2 * 152 + tiles - 1) / tiles, nch / 8));
+  if ((size_t)nsplit * na * nb > work_cap) nsplit = 1;
+  const int per = (nch + nsplit - 1) / nsplit;
+  nsplit = (nch + per - 1) / per;
+  if (nsplit == 1) {
+    launch("gram", 32, k_gram_tc, dim3(tiles, 1), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, nu, out, nb, per, (size_t)0,
+           err);
+  } else {
+    const size_t stride = (size_t)na * nb;
+    launch("gram", 32, k_gram_tc, dim3(tiles, nsplit), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, nu, work, nb, per,
+           stride, err);
+    WDF_CUDA_TRY(cudaGetLastError());
+    launch("gram_sum", 0, k_tc_sum_splits, dim3((unsigned)(((size_t)na * nb + 255) / 256)), dim3(256), 0, st, (const double *)work,
+           nsplit, stride, out, na, nb, nb);
+  }
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc, const double *d, int na, float *chi, float *clo,
+                       const float *uth, const float *utl, float c0, const float *P, double *part, int *err, cudaStream_t st) {
+  if (ny <= 0) return;
+  const int kp = tc_rows(na);
+  launch("lincomb", 32, k_tc_coef, dim3((ny + 31) / 32, (kp + 31) / 32), dim3(32, 8), 0, st, S, ldc, d, na, ny, kp, chi, clo);
+  WDF_CUDA_TRY(cudaGetLastError());
+  const int ntile = (2 * g.nint + 255) / 256;
+  launch("lincomb", 32, k_lincomb_tc, dim3((ny + TM - 1) / TM, ntile), dim3(256), lincomb_tc_smem(), st, g, Y, ny, (const float *)chi,
+         (const float *)clo, kp, uth, utl, c0, P, part, lincomb_dot_chunks(g), err);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace wdf

@@ -22,7 +22,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "wdf.h")
 WDF_OK, WDF_EINVAL, WDF_ENOMEM, WDF_ECUDA, WDF_ENOCONV, WDF_ETIMEOUT, WDF_ENAN, WDF_ESTATE = range(8)
 WDF_MEM_HOST, WDF_MEM_DEVICE = 0, 1
 WDF_FP64, WDF_MIXED, WDF_MIXED_DF = 0, 1, 2
-WDF_PRECOND_NONE, WDF_PRECOND_TPA = 0, 1
+WDF_PRECOND_NONE, WDF_PRECOND_TPA, WDF_PRECOND_LEARNED = 0, 1, 2
+MODEL_NPARAM, MODEL_FLOATS = 4610, 4618
 
 
 class WdfError(RuntimeError):
@@ -70,6 +71,7 @@ class _Options(ctypes.Structure):
         ("gs_extra", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int),
+        ("warm_start", ctypes.c_int),
     ]
 
 
@@ -83,6 +85,24 @@ class Stats(ctypes.Structure):
         ("napply", ctypes.c_int64),
         ("davidson_iters", ctypes.c_int32),
         ("converged", ctypes.c_int32),
+        ("ms", ctypes.c_double),
+        ("fallbacks", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("lr", ctypes.c_double), ("npert", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class TrainStats(ctypes.Structure):
+    _fields_ = [
+        ("nsamples", ctypes.c_int64),
+        ("steps", ctypes.c_int32),
+        ("loss_first", ctypes.c_double),
+        ("loss_last", ctypes.c_double),
         ("ms", ctypes.c_double),
     ]
 
@@ -112,6 +132,20 @@ def load(path: str = LIB_PATH):
         "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
         "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
         "wdf_apply_hamiltonian_noalloc": (I, [P, I, P, P]),
+        "wdf_default_train_opts": (None, [P]),
+        "wdf_model_create": (I, [I, ctypes.c_uint64, ctypes.POINTER(P)]),
+        "wdf_model_free": (None, [P]),
+        "wdf_model_set_weights": (I, [P, P]),
+        "wdf_model_get_weights": (I, [P, P]),
+        "wdf_model_add_solves": (I, [P, P, I, P, I, P]),
+        "wdf_model_num_samples": (ctypes.c_int64, [P]),
+        "wdf_model_set_samples": (I, [P, ctypes.c_int64, P, P, P]),
+        "wdf_model_get_samples": (I, [P, ctypes.c_int64, ctypes.c_int64, P, P, P]),
+        "wdf_model_loss_grad": (I, [P, P, P]),
+        "wdf_model_train": (I, [P, P, P]),
+        "wdf_model_predict": (I, [P, ctypes.c_int64, P, P]),
+        "wdf_set_model": (I, [P, P]),
+        "wdf_train_preconditioner": (I, [P, I, P, ctypes.POINTER(P), P]),
         "wdf_profile_kernel": (I, [P, ctypes.c_char_p]),
         "wdf_profile_read": (I, [P, P, P]),
         "wdf_launch_count": (ctypes.c_int64, []),
@@ -177,7 +211,7 @@ class Context:
     def __init__(self, system, psi=None, eps=None, precision: str = "mixed", precond: str = "tpa", cg_tol: float = 1e-8,
                  cg_maxiter: int = 1000, inner_tol: float = 1e-5, alpha: float = 0.0, max_batch: int = 0,
                  gs_tol: float = 1e-10, gs_maxiter: int = 300, gs_extra: int = 8, stream: Optional[int] = None,
-                 device: int = 0, data_on_device: bool = False):
+                 device: int = 0, data_on_device: bool = False, warm_start: bool = False):
         self._lib = load()
         self._ctx = ctypes.c_void_p()
         opt = _Options()
@@ -188,6 +222,7 @@ class Context:
         opt.max_batch, opt.gs_tol, opt.gs_maxiter, opt.gs_extra = max_batch, gs_tol, gs_maxiter, gs_extra
         opt.stream = stream
         opt.device = device
+        opt.warm_start = 1 if warm_start else 0
         keep: list = []
         s = _System()
         s.cell[:] = [float(v) for v in np.asarray(system.cell, dtype=np.float64).reshape(9)]
@@ -337,3 +372,113 @@ class Context:
                                          ctypes.byref(st))
         self._check(rc, (lam, vec, st))
         return lam, vec, st
+
+    def set_model(self, model: Optional["Model"]):
+        """Use a trained model as preconditioner (WDF_PRECOND_LEARNED); None: back to TPA."""
+        self._check(self._lib.wdf_set_model(self._ctx, model._m if model is not None else None))
+
+
+def _check_global(lib, rc, obj=None):
+    if rc != WDF_OK:
+        raise WdfError(rc, lib.wdf_last_error(None).decode())
+
+
+class Model:
+    """A learned-preconditioner model on one GPU (wdf_model_*; layout in include/wdf.h)."""
+
+    def __init__(self, device: int = 0, seed: int = 0, _handle=None):
+        self._lib = load()
+        self._m = ctypes.c_void_p()
+        if _handle is not None:
+            self._m = _handle
+        else:
+            _check_global(self._lib, self._lib.wdf_model_create(device, seed, ctypes.byref(self._m)))
+
+    def close(self):
+        if getattr(self, "_m", None) and self._m.value:
+            self._lib.wdf_model_free(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        _check_global(self._lib, rc)
+
+    @property
+    def weights(self) -> np.ndarray:
+        w = np.empty(MODEL_FLOATS, dtype=np.float32)
+        self._check(self._lib.wdf_model_get_weights(self._m, w.ctypes.data))
+        return w
+
+    @weights.setter
+    def weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32).reshape(MODEL_FLOATS)
+        self._check(self._lib.wdf_model_set_weights(self._m, a.ctypes.data))
+
+    def add_solves(self, ctx: Context, phi):
+        """Append the samples of TPA solves of chi0bar phi on ctx; returns the Stats."""
+        keep: list = []
+        p, mem = _ptr_in(phi, np.complex128, keep)
+        st = Stats()
+        rc = self._lib.wdf_model_add_solves(self._m, ctx._ctx, int(phi.shape[0]), p, mem, ctypes.byref(st))
+        if rc not in (WDF_OK, WDF_ENOCONV):
+            self._check(rc)
+        return st
+
+    @property
+    def num_samples(self) -> int:
+        return int(self._lib.wdf_model_num_samples(self._m))
+
+    def set_samples(self, feat, tgt, wt):
+        f = np.ascontiguousarray(feat, dtype=np.float32).reshape(-1, 4)
+        t = np.ascontiguousarray(tgt, dtype=np.float32).reshape(-1, 2)
+        w = np.ascontiguousarray(wt, dtype=np.float32).reshape(-1, 2)
+        if not (f.shape[0] == t.shape[0] == w.shape[0]):
+            raise ValueError("features, targets and weights must have one row per sample")
+        self._check(self._lib.wdf_model_set_samples(self._m, f.shape[0], f.ctypes.data, t.ctypes.data, w.ctypes.data))
+
+    def samples(self, first: int = 0, count: Optional[int] = None):
+        """(features[n, 4], targets[n, 2], weights[n, 2]) as float32 arrays."""
+        n = self.num_samples - first if count is None else count
+        f = np.empty((n, 4), dtype=np.float32)
+        t = np.empty((n, 2), dtype=np.float32)
+        w = np.empty((n, 2), dtype=np.float32)
+        self._check(self._lib.wdf_model_get_samples(self._m, first, n, f.ctypes.data, t.ctypes.data, w.ctypes.data))
+        return f, t, w
+
+    def loss_grad(self):
+        g = np.empty(MODEL_NPARAM)
+        loss = ctypes.c_double()
+        self._check(self._lib.wdf_model_loss_grad(self._m, ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, steps: int = 600, lr: float = 3e-3) -> TrainStats:
+        o = TrainOpts()
+        self._lib.wdf_default_train_opts(ctypes.byref(o))
+        o.steps, o.lr = steps, lr
+        st = TrainStats()
+        self._check(self._lib.wdf_model_train(self._m, ctypes.byref(o), ctypes.byref(st)))
+        return st
+
+    def predict(self, feat) -> np.ndarray:
+        f = np.ascontiguousarray(feat, dtype=np.float32).reshape(-1, 4)
+        out = np.empty((f.shape[0], 2), dtype=np.float32)
+        self._check(self._lib.wdf_model_predict(self._m, f.shape[0], f.ctypes.data, out.ctypes.data))
+        return out
+
+
+def train_preconditioner(contexts, npert: int = 8, steps: int = 600, lr: float = 3e-3, seed: int = 0):
+    """wdf_train_preconditioner over a list of contexts: returns (Model, TrainStats)."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(contexts))(*[c._ctx.value for c in contexts])
+    o = TrainOpts()
+    lib.wdf_default_train_opts(ctypes.byref(o))
+    o.steps, o.lr, o.npert, o.seed = steps, lr, npert, seed
+    h = ctypes.c_void_p()
+    st = TrainStats()
+    _check_global(lib, lib.wdf_train_preconditioner(arr, len(contexts), ctypes.byref(o), ctypes.byref(h), ctypes.byref(st)))
+    return Model(_handle=h), st

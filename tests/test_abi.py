@@ -38,7 +38,9 @@ def test_struct_layouts_match_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     probes = []
-    for cname, py in (("wdf_system", wdf._System), ("wdf_options", wdf._Options), ("wdf_stats", wdf.Stats)):
+    mirrors = (("wdf_system", wdf._System), ("wdf_options", wdf._Options), ("wdf_stats", wdf.Stats),
+               ("wdf_train_opts", wdf.TrainOpts), ("wdf_train_stats", wdf.TrainStats))
+    for cname, py in mirrors:
         probes.append(f'printf("%zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
             probes.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
@@ -49,7 +51,7 @@ def test_struct_layouts_match_header(tmp_path):
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = []
-    for py in (wdf._System, wdf._Options, wdf.Stats):
+    for _, py in mirrors:
         want.append(ctypes.sizeof(py))
         want.extend(getattr(py, f).offset for f, _ in py._fields_)
     assert got == want
@@ -63,7 +65,10 @@ def test_strerror_and_defaults(lib):
     o = wdf._Options()
     lib.wdf_default_options(ctypes.byref(o))
     assert o.precision == wdf.WDF_MIXED and o.precond == wdf.WDF_PRECOND_TPA
-    assert o.cg_tol == 1e-8 and o.cg_maxiter == 1000 and o.inner_tol == 1e-5
+    assert o.cg_tol == 1e-8 and o.cg_maxiter == 1000 and o.inner_tol == 1e-5 and o.warm_start == 0
+    t = wdf.TrainOpts()
+    lib.wdf_default_train_opts(ctypes.byref(t))
+    assert t.steps == 600 and t.lr == 3e-3 and t.npert == 8 and t.seed == 0
 
 
 def test_null_arguments_are_rejected(lib):
@@ -72,6 +77,22 @@ def test_null_arguments_are_rejected(lib):
     assert lib.wdf_setup_hamiltonian(None, None, None) == wdf.WDF_EINVAL
     assert lib.wdf_apply_chi0(None, 1, None, None, None, 0, None) == wdf.WDF_EINVAL
     lib.wdf_destroy(None)  # ignored
+    assert lib.wdf_model_num_samples(None) == -1
+    assert lib.wdf_model_loss_grad(None, None, None) == wdf.WDF_EINVAL
+    assert lib.wdf_set_model(None, None) == wdf.WDF_EINVAL
+    assert lib.wdf_model_create(0, 0, None) == wdf.WDF_EINVAL
+    lib.wdf_model_free(None)  # ignored
+
+
+def test_model_layout_constants_match_header():
+    import re
+
+    from paper_2607_14025_gb300 import wdf
+    from oracle import mlp
+
+    text = open(wdf.HEADER).read()
+    assert int(re.search(r"#define WDF_MODEL_NPARAM (\d+)", text).group(1)) == wdf.MODEL_NPARAM == mlp.NPARAM
+    assert int(re.search(r"#define WDF_MODEL_FLOATS (\d+)", text).group(1)) == wdf.MODEL_FLOATS == mlp.NMODEL
 
 
 def test_without_gpu_setup_reports_state_error():
