@@ -223,8 +223,7 @@ def run_gpu(args):
                       max_batch=args.max_batch)
     t_setup = time.perf_counter() - t_setup
     eps, _ = ctx.orbitals()
-    train_info = None
-    if args.precond == "learned":
+    def train_learned():
         # train on other seeds of the same system family (the benchmarked system is seed 0)
         t_tr = time.perf_counter()
         fam = [wdf.Context(synth.make_system(dataclasses.replace(synth.spec(WORKLOAD), seed=k)), precision=args.precision, cg_tol=1e-8,
@@ -233,10 +232,12 @@ def run_gpu(args):
         for c in fam:
             c.close()
         ctx.set_model(model)
-        train_info = {"systems": f"{WORKLOAD} family, seeds 1..{args.train_systems} (benchmarked system: seed 0)",
-                      "perturbations_per_system": args.train_npert, "samples": ts.nsamples, "adam_steps": ts.steps,
-                      "loss_first": ts.loss_first, "loss_last": ts.loss_last, "train_ms": ts.ms,
-                      "wall_s_incl_ground_states": time.perf_counter() - t_tr}
+        return {"systems": f"{WORKLOAD} family, seeds 1..{args.train_systems} (benchmarked system: seed 0)",
+                "perturbations_per_system": args.train_npert, "samples": ts.nsamples, "adam_steps": ts.steps,
+                "loss_first": ts.loss_first, "loss_last": ts.loss_last, "train_ms": ts.ms,
+                "wall_s_incl_ground_states": time.perf_counter() - t_tr}
+
+    train_info = train_learned() if args.precond == "learned" else None
     phi_d = torch.from_numpy(phi_h).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -285,6 +286,7 @@ def run_gpu(args):
         clocks = clk.stop()
         launches = (wdf.launch_count() - nl0) / args.steps
         k_launches, k_ms = ctx.profile_read()
+        k_blocks = ctx.profile_units()  # (pair, z plane) blocks of the timed plane launches
         ctx.profile_kernel(None)
         ms_dev = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         # end to end through the C ABI with host buffers
@@ -294,6 +296,27 @@ def run_gpu(args):
             lam_h, vec_h, st_h = step(phi_h)
         torch.cuda.synchronize(dev)
         ms_e2e = 1e3 * (time.perf_counter() - t0) / args.steps
+    learned_line = None
+    if args.precond == "tpa" and args.with_learned and world == 1:
+        # the same step with the learned preconditioner (trained here, not timed), same protocol
+        info = train_learned()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                flush.fill_(1.0)
+                step(phi_d)
+            torch.cuda.synchronize(dev)
+            evl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.fill_(1.0)
+                evl[i][0].record(stream)
+                _, _, stl = step(phi_d)
+                evl[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+        ms_l = sum(a.elapsed_time(b) for a, b in evl) / args.steps
+        dl = stl.as_dict()
+        learned_line = {"value": job_throughput(world, dl["nsolve"], ms_l), "unit": UNIT, "ms_per_step": ms_l,
+                        "cg_iters_per_solve": dl["cg_iters"] / max(1, dl["nsolve"]), "cg_iters_max": dl["cg_iters_max"],
+                        "max_residual": dl["max_residual"], "fallbacks_per_step": dl["fallbacks"], "training": info}
     ms_dev, ms_e2e = reduce_step_times([ms_dev, ms_e2e], device=dev)
     nsolve = stats[-1]["nsolve"]
     iters = stats[-1]["cg_iters"] / max(1, nsolve)
@@ -303,11 +326,14 @@ def run_gpu(args):
     if rank != 0:
         return
     hbm, bf16, src = peaks()
-    # algorithmic flops of one launch of the dominant kernel (FFT convention)
-    npair = NPERT * s.nocc // 2
-    per_launch_flops = plane_flops(s, npair)
+    # algorithmic flops of the dominant kernel over its timed launches (FFT convention, see
+    # the design doc): per (pair, z plane) block, times the blocks launched (compaction shrinks the
+    # later launches, so the per-launch work varies)
+    per_plane_flops = plane_flops(s, 1) / s.grid[2]
+    total_flops = per_plane_flops * k_blocks
     avg_ms = k_ms / max(1, k_launches)
-    achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12 if k_launches else None
+    per_launch_flops = total_flops / max(1, k_launches)
+    achieved = total_flops / (k_ms * 1e-3) / 1e12 if k_launches else None
     alu_peak = ALU_PEAK_TFLOPS[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -320,6 +346,7 @@ def run_gpu(args):
                    "parallelism": f"perturbation blocks x{world}"},
         "chi0_applies_per_s": job_throughput(world, NPERT, ms_dev),
         "cg_iters_per_solve": iters,
+        "cg_iters_max": stats[-1]["cg_iters_max"],
         "max_residual": stats[-1]["max_residual"],
         "fallbacks_per_step": stats[-1]["fallbacks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,
@@ -329,6 +356,7 @@ def run_gpu(args):
                      "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
                      "launches_per_step": k_launches / args.steps, "ms_per_launch": avg_ms,
                      "share_of_step": k_ms / args.steps / ms_dev, "algorithmic_flops_per_launch": per_launch_flops,
+                     "flops_per_pair_plane": per_plane_flops, "pair_planes_per_step": k_blocks / args.steps,
                      "peak_source": ALU_PEAK_SOURCE[args.precision]},
         "clocks": clocks,
         "peaks_source": src,
@@ -337,6 +365,8 @@ def run_gpu(args):
     }
     if train_info:
         line["learned_preconditioner"] = train_info
+    if learned_line:
+        line["learned_preconditioner"] = learned_line
     if args.cpu_baseline:
         sys_o, R, phi1, t_gs = oracle_sample(WORKLOAD)
         t0 = time.time()
@@ -364,6 +394,8 @@ def main():
     ap.add_argument("--npert", type=int, default=128, help="perturbations per block (default 128)")
     ap.add_argument("--precond", choices=["tpa", "learned"], default="tpa",
                     help="learned: train the MLP preconditioner on other seeds of the family first (not timed)")
+    ap.add_argument("--no-learned", dest="with_learned", action="store_false",
+                    help="skip the extra timing of the learned preconditioner after the TPA headline")
     ap.add_argument("--train-systems", type=int, default=4)
     ap.add_argument("--train-npert", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=600)

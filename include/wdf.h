@@ -287,6 +287,11 @@ int wdf_profile_kernel(wdf_ctx *ctx, const char *kernel);
  * milliseconds. Synchronises the context's stream. */
 int wdf_profile_read(wdf_ctx *ctx, int64_t *launches, double *ms);
 
+/* Thread blocks launched by the timed launches of the selected class since wdf_profile_kernel:
+ * the work units of kernels that give each block one unit (plane_vloc: one block per pair of
+ * solves and z plane). Does not synchronise. */
+int wdf_profile_units(wdf_ctx *ctx, int64_t *blocks);
+
 /* Number of kernel launches the library has made in this process so far (all contexts). */
 int64_t wdf_launch_count(void);
 

@@ -168,6 +168,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   upload(c, c->t_xact, L.xact);
   upload(c, c->t_xactn, L.xactn);
   upload(c, c->t_jidx, L.jidx);
+  upload(c, c->t_jnat, L.jnat);
   upload(c, c->t_pos3, L.pos3);
   upload(c, c->t_g2, L.g2);
   upload(c, c->t_vhalf, L.vhalf);
@@ -235,6 +236,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
     c->fdf.tw3 = tdf + 2 * kMaxN;
   }
   c->f64.jidx = c->f32.jidx = c->fdf.jidx = (std::getenv("WDF_GENERIC_PLANE") ? nullptr : c->t_jidx.as<int>());
+  c->f64.jnat = c->f32.jnat = c->fdf.jnat = c->t_jnat.as<int>();
   c->f64.tw1 = t64;
   c->f64.tw2 = t64 + kMaxN;
   c->f64.tw3 = t64 + 2 * kMaxN;
@@ -399,7 +401,7 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->thr,       &c->gramw,     &c->xpert,   &c->dvgrid,  &c->accgrid, &c->cb2,      &c->outi,     &c->drhoi,
                   &c->ext_in,    &c->ext_out,   &c->ext_out2, &c->dv_V,   &c->dv_W,    &c->dv_X,     &c->dv_AX,    &c->dv_R,
                   &c->dv_H,      &c->dv_Y,      &c->dv_theta, &c->dv_jac, &c->dv_jint, &c->dv_small, &c->dv_neg,   &c->zeros,
-                  &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho, &c->t_xactn, &c->t_jidx,
+                  &c->flag,      &c->guess,     &c->chi_out, &c->chi_drho, &c->t_xactn, &c->t_jidx, &c->t_jnat,
                   &c->t_twdf,    &c->vlocdf,    &c->Udf,     &c->psirdf,   &c->dfa,     &c->dfb,
                   &c->xpdf,      &c->dvgriddf,  &c->accgriddf, &c->cb2df,  &c->drdf,    &c->oudf, &c->chol,
                   &c->ml64,      &c->ml32,      &c->mlw64,   &c->krow,     &c->rr_ref,  &c->it_ref,  &c->nfb,
@@ -407,7 +409,8 @@ void wdf_destroy(wdf_ctx *c) {
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {
-    DBuf *cb[] = {&w->r, &w->z, &w->p, &w->Ap, &w->x, &w->cb, &w->S, &w->part1, &w->part2, &w->part3, &w->dbl, &w->ints};
+    DBuf *cb[] = {&w->r,     &w->z,     &w->p,     &w->Ap, &w->x,  &w->cb, &w->S,  &w->part1,
+                  &w->part2, &w->part3, &w->dbl, &w->ints, &w->r2, &w->p2, &w->cd, &w->ci, &w->cidx};
     for (DBuf *b : cb) b->release();
   }
   delete c;
@@ -517,6 +520,7 @@ int wdf_profile_kernel(wdf_ctx *c, const char *kernel) {
     if (c->st) WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->prof.used = 0;
     c->prof.count = 0;
+    c->prof.blocks = 0;
     c->prof_on = kernel != nullptr;
     if (!kernel) return WDF_OK;
     std::string k(kernel);
@@ -547,6 +551,12 @@ int wdf_profile_read(wdf_ctx *c, int64_t *launches, double *ms) {
     *ms = tot;
     return WDF_OK;
   });
+}
+
+int wdf_profile_units(wdf_ctx *c, int64_t *blocks) {
+  if (!c || !blocks) return WDF_EINVAL;
+  *blocks = c->prof.blocks;
+  return WDF_OK;
 }
 
 int64_t wdf_launch_count(void) { return (int64_t)g_launches.load(); }

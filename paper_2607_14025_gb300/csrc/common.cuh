@@ -122,6 +122,7 @@ struct Profiler {
   std::vector<cudaEvent_t> ev;
   size_t used = 0;
   long long count = 0;
+  long long blocks = 0;  // thread blocks of the timed launches (the work units of per-block kernels)
 };
 extern thread_local Profiler *t_prof;
 extern std::atomic<long long> g_launches;
@@ -140,6 +141,7 @@ inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, di
   if (timed) {
     prof_record(st);
     ++t_prof->count;
+    t_prof->blocks += (long long)grid.x * grid.y * grid.z;
   }
 }
 

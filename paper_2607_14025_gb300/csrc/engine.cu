@@ -48,6 +48,94 @@ __global__ void k_sum_chunks(const double *__restrict__ part, int n, int nchunk,
 static int grid_for(size_t tot) { return (int)std::min<size_t>(8192, (tot + 255) / 256); }
 
 // ---------------------------------------------------------------------------------------------
+// compaction of the active solves of a CG batch
+
+// per-solve state that moves with the rows (krow: preconditioner row; home: row of the caller's x,
+// -1 for a padding row; rr_ref, it_ref, vorig: learned preconditioner only, may be null)
+struct CgRows {
+  double *rz, *rz_new, *thr, *shift, *rr_ref;
+  int *active, *iters, *krow, *vorig, *it_ref, *home;
+};
+
+// src[k] = the k-th active row, in increasing order (one block of 1024 threads, chunked scan)
+__global__ void __launch_bounds__(1024) k_compact_index(const int *__restrict__ active, int n, int *__restrict__ src) {
+  __shared__ int sums[1024];
+  const int t = threadIdx.x, per = (n + 1023) / 1024;
+  const int b = min(n, t * per), e = min(n, b + per);
+  int c = 0;
+  for (int i = b; i < e; ++i) c += active[i] ? 1 : 0;
+  sums[t] = c;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int v = t >= off ? sums[t - off] : 0;
+    __syncthreads();
+    sums[t] += v;
+    __syncthreads();
+  }
+  int pos = sums[t] - c;
+  for (int i = b; i < e; ++i)
+    if (active[i]) src[pos++] = i;
+}
+
+__global__ void k_compact_scalars(CgRows a, CgRows b, const int *__restrict__ src, int nnew, int nact) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnew) return;
+  if (k < nact) {
+    const int i = src[k];
+    b.rz[k] = a.rz[i];
+    b.rz_new[k] = a.rz_new[i];
+    b.thr[k] = a.thr[i];
+    b.shift[k] = a.shift[i];
+    if (b.rr_ref) b.rr_ref[k] = a.rr_ref[i];
+    b.active[k] = a.active[i];
+    b.iters[k] = a.iters[i];
+    b.krow[k] = a.krow[i];
+    if (b.vorig) b.vorig[k] = a.vorig[i];
+    if (b.it_ref) b.it_ref[k] = a.it_ref[i];
+    b.home[k] = a.home ? a.home[i] : i;
+  } else {  // padding row that completes the last pair: inactive, zero vectors
+    b.rz[k] = 1.0;
+    b.rz_new[k] = 0.0;
+    b.thr[k] = 1e300;
+    b.shift[k] = 0.0;
+    if (b.rr_ref) b.rr_ref[k] = 0.0;
+    b.active[k] = 0;
+    b.iters[k] = 0;
+    b.krow[k] = a.krow[0];
+    if (b.vorig) b.vorig[k] = 0;
+    if (b.it_ref) b.it_ref[k] = 0;
+    b.home[k] = -1;
+  }
+}
+
+template <typename T>
+__global__ void k_compact_vectors(Geo g, const cplx<T> *__restrict__ r, const cplx<T> *__restrict__ p, cplx<T> *__restrict__ r2,
+                                  cplx<T> *__restrict__ p2, const int *__restrict__ src, int nnew, int nact) {
+  const size_t tot = (size_t)nnew * g.ld;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / g.ld), e = (int)(t % g.ld);
+    if (k < nact) {
+      const size_t o = (size_t)src[k] * g.ld + e;
+      r2[t] = r[o];
+      p2[t] = p[o];
+    } else {
+      r2[t] = mkc<T>(0, 0);
+      p2[t] = mkc<T>(0, 0);
+    }
+  }
+}
+
+// iteration counts (and preconditioner rows) of the current rows back to the caller's order
+__global__ void k_scatter_home(CgRows a, int n, int *__restrict__ iters_home, int *__restrict__ krow_home) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int h = a.home ? a.home[k] : k;
+  if (h < 0) return;
+  iters_home[h] = a.iters[k];
+  if (krow_home) krow_home[h] = a.krow[k];
+}
+
+// ---------------------------------------------------------------------------------------------
 // precision traits
 
 template <typename T> struct Prec;
@@ -278,29 +366,86 @@ static void cg_solve(wdf_ctx *c, const cplx<T> *b, cplx<T> *x, int n, int maxite
   int nact = 0;
   WDF_CUDA_TRY(cudaMemcpyAsync(&nact, s.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
   WDF_CUDA_TRY(cudaStreamSynchronize(st));
+  // Rows of the batch: the home set (the caller's order) and two compacted sets. When enough
+  // solves have converged, the active ones are gathered into a dense prefix (r, p and the
+  // per-solve state; x stays in the caller's order and is reached through home[]), so the FFTs
+  // and projections of later iterations only touch solves that still iterate.
+  const bool learned = s.krow != nullptr;
+  static const bool compaction = std::getenv("WDF_NO_COMPACT") == nullptr;
+  CgRows cur{s.rz, s.rz_new, s.thr, s.shift, s.rr_ref, s.active, s.iters, s.vidx, const_cast<int *>(s.vorig), s.it_ref, nullptr};
+  int ncur = n, nset = 0;
+  w.r2.ensure(vb);
+  w.p2.ensure(vb);
+  cplx<T> *rB = w.r2.as<cplx<T>>(), *pB = w.p2.as<cplx<T>>();
+  auto compact = [&]() {
+    const int nnew = nact + (nact & 1);
+    w.cidx.ensure(sizeof(int) * (size_t)n);
+    w.cd.ensure(sizeof(double) * 5 * 2 * (size_t)n);
+    w.ci.ensure(sizeof(int) * 6 * 2 * (size_t)n);
+    const int set = nset == 1 ? 2 : 1;
+    double *dd = w.cd.as<double>() + (size_t)(set - 1) * 5 * n;
+    int *di = w.ci.as<int>() + (size_t)(set - 1) * 6 * n;
+    CgRows nx{dd, dd + n, dd + 2 * (size_t)n, dd + 3 * (size_t)n, learned ? dd + 4 * (size_t)n : nullptr,
+              di, di + n, di + 2 * (size_t)n, learned ? di + 3 * (size_t)n : nullptr, learned ? di + 4 * (size_t)n : nullptr,
+              di + 5 * (size_t)n};
+    int *src = w.cidx.as<int>();
+    if (nset > 0)  // counts (and TPA-fallback rows) of the solves about to be dropped
+      launch("compact", 0, k_scatter_home, dim3((ncur + 127) / 128), dim3(128), 0, st, cur, ncur, ii + n,
+             learned ? c->krow.as<int>() : nullptr);
+    launch("compact", 0, k_compact_index, dim3(1), dim3(1024), 0, st, (const int *)cur.active, ncur, src);
+    launch("compact", 0, k_compact_scalars, dim3((nnew + 127) / 128), dim3(128), 0, st, cur, nx, (const int *)src, nnew, nact);
+    launch("compact", bits_of<T>(), k_compact_vectors<T>, dim3(grid_for((size_t)nnew * g.ld)), dim3(256), 0, st, g,
+           (const cplx<T> *)r, (const cplx<T> *)p, rB, pB, (const int *)src, nnew, nact);
+    WDF_CUDA_TRY(cudaGetLastError());
+    std::swap(r, rB);
+    std::swap(p, pB);
+    cur = nx;
+    ncur = nnew;
+    nset = set;
+    s.rz = cur.rz;
+    s.rz_new = cur.rz_new;
+    s.thr = cur.thr;
+    s.shift = cur.shift;
+    s.active = cur.active;
+    s.iters = cur.iters;
+    s.vidx = cur.krow;
+    s.home = cur.home;
+    if (learned) {
+      s.krow = cur.krow;
+      s.vorig = cur.vorig;
+      s.rr_ref = cur.rr_ref;
+      s.it_ref = cur.it_ref;
+    }
+  };
   PDir<T> dir;
-  dir.p = p;
-  dir.r = r;
   dir.K = K;
-  dir.vidx = s.vidx;
-  dir.active = s.active;
-  dir.beta = s.rz_new;
   for (int it = 0; it < maxiter && nact > 0; ++it) {
+    if (compaction && nact <= ncur - std::max(8, ncur / 8)) compact();
+    dir.p = p;
+    dir.r = r;
+    dir.vidx = s.vidx;
+    dir.active = s.active;
+    dir.beta = s.rz_new;
     // p = K r + beta p (from the second iteration on), A p and the partial sums of <p, A p>
-    int ndot = apply_operator_cg<T>(c, p, Ap, n, s.shift, it > 0 ? &dir : nullptr, s.part1);
+    int ndot = apply_operator_cg<T>(c, p, Ap, ncur, s.shift, it > 0 ? &dir : nullptr, s.part1);
     if (ndot == 0) {
-      launch_dot_partial<T>(g, p, Ap, n, s.part1, nch, st);
+      launch_dot_partial<T>(g, p, Ap, ncur, s.part1, nch, st);
       ndot = nch;
     }
-    launch_cg_scalars(s, n, ndot, 0, maxiter, st);
-    launch_cg_update<T>(g, x, r, nullptr, p, Ap, K, s, n, nch, st);
+    launch_cg_scalars(s, ncur, ndot, 0, maxiter, st);
+    launch_cg_update<T>(g, x, r, nullptr, p, Ap, K, s, ncur, nch, st);
     WDF_CUDA_TRY(cudaMemsetAsync(s.nactive, 0, sizeof(int), st));
-    launch_cg_scalars(s, n, nch, 1, maxiter, st);
+    launch_cg_scalars(s, ncur, nch, 1, maxiter, st);
     WDF_CUDA_TRY(cudaMemcpyAsync(&nact, s.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     WDF_CUDA_TRY(cudaStreamSynchronize(st));
   }
+  if (nset > 0) {
+    launch("compact", 0, k_scatter_home, dim3((ncur + 127) / 128), dim3(128), 0, st, cur, ncur, ii + n,
+           learned ? c->krow.as<int>() : nullptr);
+    WDF_CUDA_TRY(cudaGetLastError());
+  }
   iters.resize(n);
-  WDF_CUDA_TRY(cudaMemcpyAsync(iters.data(), s.iters, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  WDF_CUDA_TRY(cudaMemcpyAsync(iters.data(), ii + n, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
   WDF_CUDA_TRY(cudaStreamSynchronize(st));
 }
 

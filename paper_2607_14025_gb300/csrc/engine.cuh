@@ -23,7 +23,7 @@ struct Layout {
   std::vector<int> col_n1, col_n2, col_zlo, col_off;
   std::vector<int> e_col, e_z;
   std::vector<double> g2, vhalf;
-  std::vector<int> tile_idx, xact, xactn, jidx;
+  std::vector<int> tile_idx, xact, xactn, jidx, jnat;  // jnat: natural y * n1 + x of each disk column
   int xmax = 0;
   std::vector<short> pos3;
   std::vector<int> emap, emap2, econj;  // external half-sphere index -> internal element
@@ -61,7 +61,7 @@ struct wdf_ctx {
 
   // layout tables
   wdf::DBuf t_col_off, t_col_zlo, t_e_col, t_e_z, t_tile, t_xact, t_pos3, t_g2, t_vhalf;
-  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32, t_twdf, t_xactn, t_jidx;
+  wdf::DBuf t_emap, t_emap2, t_econj, t_tw64, t_tw32, t_twdf, t_xactn, t_jidx, t_jnat;
 
   // operator data
   wdf::DBuf vloc64, vloc32;  // V_loc on the grid
@@ -76,6 +76,7 @@ struct wdf_ctx {
   // workspaces (grow-only)
   struct Cg {
     wdf::DBuf r, z, p, Ap, x, cb, S, part1, part2, part3, dbl, ints;
+    wdf::DBuf r2, p2, cd, ci, cidx;  // compacted copies of the active solves' rows and state
   } cg64, cg32, cgdf;
   // learned preconditioner (wdf_set_model): [2 nocc][ld] tables (learned rows, then TPA rows),
   // first-iterate gains [nocc][ld]; per-solve row index, stall-check state and fallback counter

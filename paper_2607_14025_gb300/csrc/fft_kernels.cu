@@ -118,6 +118,11 @@ __global__ void __launch_bounds__(kThreads) k_zpass_r2g(const cplx<T> *__restric
   const int sa = 2 * q, sb = 2 * q + 1;
   const bool hasb = sb < nvec;
   const T sc = ea.scale;
+  T sha = 0, shb = 0;  // per-vector shifts, converted once (the stores below may alias the array)
+  if (EPI == EPI_HSHIFT) {
+    sha = (T)ea.shift[sa];
+    if (hasb) shb = (T)ea.shift[sb];
+  }
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int k = g.e_col[e], c = k - k0, z = g.e_z[e];
     const cplx<T> g1 = sm[c * pitch + g.pos3[wrap(z, n3)]];
@@ -133,12 +138,12 @@ __global__ void __launch_bounds__(kThreads) k_zpass_r2g(const cplx<T> *__restric
       const T kin = (T)(0.5 * g.g2[e]);
       {
         const cplx<T> xv = ea.X[(size_t)sa * g.ld + e];
-        const T d = kin - (T)ea.shift[sa];
+        const T d = kin - sha;
         ea.Y[(size_t)sa * g.ld + e] = mkc<T>(a.x + d * xv.x, a.y + d * xv.y);
       }
       if (hasb) {
         const cplx<T> xv = ea.X[(size_t)sb * g.ld + e];
-        const T d = kin - (T)ea.shift[sb];
+        const T d = kin - shb;
         ea.Y[(size_t)sb * g.ld + e] = mkc<T>(b.x + d * xv.x, b.y + d * xv.y);
       }
     } else {  // EPI_DRHO: Y = drho, Y2 = v^1/2 drho

@@ -16,6 +16,7 @@ template <typename T> struct FftCtx {
   Plan1D P1, P2, P3;
   const cplx<T> *tw1, *tw2, *tw3;  // exp(2 pi i t / n) per axis
   const int *jidx;                 // [n2][n1] disk column at natural (y, x), or -1
+  const int *jnat;                 // [ndisk] natural y * n1 + x of each disk column
 };
 
 template <typename T> struct EpiArgs {
@@ -103,6 +104,9 @@ struct CgState {
   int *it_ref = nullptr;                 // iteration of the last stall check
   double *part3 = nullptr;               // partials of <r, K_TPA r> [n * nchunk]
   int *nfb = nullptr;                    // [1] solves moved to TPA
+  // after compaction of the active solves: row i of the work arrays is solve home[i] of the
+  // caller's x (null: identity)
+  const int *home = nullptr;
 };
 
 // z = K r (TPA per orbital), p = z, and partials for <r,z>, <r,r>
@@ -172,7 +176,7 @@ void launch_mlp_samples(const Geo &g, const int *emap, int npw_h, int nocc, cons
                         cudaStream_t st);
 
 // tensor-core (tcgen05 kind::tf32, three-term split) projections of the FP32 CG (tc_gemm.cu);
-// on when WDF_TC is set in the environment (WDF_NO_TC wins)
+// on unless WDF_NO_TC is set in the environment (then the CUDA-core kernels run)
 bool tc_enabled();
 int tc_rows(int na);  // rows of U rounded up to 32 (the MMA N of the projections, <= 256)
 void set_tc_limits();

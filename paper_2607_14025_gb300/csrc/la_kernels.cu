@@ -16,6 +16,13 @@ static __device__ __forceinline__ double wgt(int e, int len0) { return e < len0 
 template <typename T> __device__ __forceinline__ double dre(cplx<T> a, cplx<T> b) {
   return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
 }
+// per-thread partial sums of the inner CG: FP32 for FP32 vectors (a thread adds a few terms; the
+// block reduction is FP64), FP64 otherwise. GB300 runs FP64 at 1/61 of the FP32 rate.
+template <typename T> using PartAcc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+template <typename T> __device__ __forceinline__ PartAcc<T> dre_acc(cplx<T> a, cplx<T> b) {
+  typedef PartAcc<T> A;
+  return (A)a.x * (A)b.x + (A)a.y * (A)b.y;
+}
 
 // block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024); result valid in
 // thread 0
@@ -344,7 +351,8 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
     }
     __syncthreads();
   }
-  double dsum[4] = {0.0, 0.0, 0.0, 0.0};
+  typedef PartAcc<T> PA;
+  PA dsum[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int s = s0 + ts * 4 + q;
@@ -364,14 +372,14 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
       *y = yv;
       if (part) {  // partial inner products <P_s, Y_s> over this block's elements
         const cplx<T> pv = P[(size_t)s * g.ld + e];
-        dsum[q] += wgt(e, g.len0) * ((double)pv.x * (double)yv.x + (double)pv.y * (double)yv.y);
+        dsum[q] += (e < g.len0 ? (PA)1 : (PA)2) * dre_acc<T>(pv, yv);
       }
     }
   }
   if (part) {  // a warp holds vectors 4 ts .. 4 ts + 3 across its 32 lanes: reduce over lanes
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      double v = dsum[q];
+      double v = (double)dsum[q];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       const int s = s0 + ts * 4 + q;
       if (te == 0 && s < ny) part[(size_t)s * gridDim.x + blockIdx.x] = v;
@@ -478,22 +486,23 @@ __global__ void __launch_bounds__(256) k_cg_start(Geo g, const cplx<T> *__restri
   const int e0 = c * DCHUNK, e1 = min(g.nint, e0 + DCHUNK);
   const size_t o = (size_t)i * g.ld;
   const T *K = kprec ? kprec + (size_t)s.vidx[i] * g.ld : nullptr;
-  double vrz = 0.0, vrr = 0.0;
+  typedef PartAcc<T> A;
+  A vrz = 0, vrr = 0;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const cplx<T> rv = r[o + e];
     const T k = K ? K[e] : (T)1;
     const cplx<T> zv = mkc<T>(k * rv.x, k * rv.y);
     if (z) z[o + e] = zv;
     p[o + e] = zv;
-    const double w = wgt(e, g.len0);
-    vrz += w * dre<T>(rv, zv);
-    vrr += w * dre<T>(rv, rv);
+    const A w = e < g.len0 ? (A)1 : (A)2;
+    vrz += w * dre_acc<T>(rv, zv);
+    vrr += w * dre_acc<T>(rv, rv);
   }
-  vrz = block_sum(vrz);
-  vrr = block_sum(vrr);
+  const double brz = block_sum((double)vrz);
+  const double brr = block_sum((double)vrr);
   if (threadIdx.x == 0) {
-    s.part1[(size_t)i * nchunk + c] = vrz;
-    s.part2[(size_t)i * nchunk + c] = vrr;
+    s.part1[(size_t)i * nchunk + c] = brz;
+    s.part2[(size_t)i * nchunk + c] = brr;
   }
 }
 
@@ -510,40 +519,42 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo g, cplx<T> *__restrict__ 
                                                   const cplx<T> *__restrict__ p, const cplx<T> *__restrict__ Ap,
                                                   const T *__restrict__ kprec, CgState s, int nchunk) {
   const int i = blockIdx.x, c = blockIdx.y;
-  double vrz = 0.0, vrr = 0.0, vr3 = 0.0;
+  typedef PartAcc<T> A;
+  A vrz = 0, vrr = 0, vr3 = 0;
   // learned table: also <r, K_TPA r> while the solve is on its learned row (for a restart)
   const bool fb = s.krow && s.krow[i] < s.nocc;
   if (s.active[i]) {
     const int e0 = c * DCHUNK, e1 = min(g.nint, e0 + DCHUNK);
-    const size_t o = (size_t)i * g.ld;
+    const size_t o = (size_t)i * g.ld, ox = (size_t)(s.home ? s.home[i] : i) * g.ld;
     const T *K = kprec ? kprec + (size_t)s.vidx[i] * g.ld : nullptr;
     const T *K3 = fb ? kprec + (size_t)(s.vorig[i] + s.nocc) * g.ld : nullptr;
     const T al = (T)(s.rz[i] / s.pap[i]);
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const cplx<T> pv = p[o + e], av = Ap[o + e];
-      cplx<T> xv = x[o + e], rv = r[o + e];
+      cplx<T> xv = x[ox + e], rv = r[o + e];
       xv.x += al * pv.x;
       xv.y += al * pv.y;
       rv.x -= al * av.x;
       rv.y -= al * av.y;
-      x[o + e] = xv;
+      x[ox + e] = xv;
       r[o + e] = rv;
       const T k = K ? K[e] : (T)1;
       const cplx<T> zv = mkc<T>(k * rv.x, k * rv.y);
       if (z) z[o + e] = zv;  // z = K r is recomputed where needed when not stored
-      const double w = wgt(e, g.len0);
-      vrz += w * dre<T>(rv, zv);
-      vrr += w * dre<T>(rv, rv);
-      if (K3) vr3 += w * (double)K3[e] * dre<T>(rv, rv);
+      const A w = e < g.len0 ? (A)1 : (A)2;
+      const A rr = dre_acc<T>(rv, rv);
+      vrz += w * dre_acc<T>(rv, zv);
+      vrr += w * rr;
+      if (K3) vr3 += w * (A)K3[e] * rr;
     }
   }
-  vrz = block_sum(vrz);
-  vrr = block_sum(vrr);
-  if (fb) vr3 = block_sum(vr3);
+  const double brz = block_sum((double)vrz);
+  const double brr = block_sum((double)vrr);
+  const double br3 = fb ? block_sum((double)vr3) : 0.0;
   if (threadIdx.x == 0) {
-    s.part1[(size_t)i * nchunk + c] = vrz;
-    s.part2[(size_t)i * nchunk + c] = vrr;
-    if (fb) s.part3[(size_t)i * nchunk + c] = vr3;
+    s.part1[(size_t)i * nchunk + c] = brz;
+    s.part2[(size_t)i * nchunk + c] = brr;
+    if (fb) s.part3[(size_t)i * nchunk + c] = br3;
   }
 }
 

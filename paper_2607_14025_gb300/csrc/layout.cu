@@ -175,6 +175,7 @@ Layout build_layout(const int32_t *miller, int npw_h, const int n[3], const doub
   const int pitch = n[0] + 1;
   L.tile_idx.resize(L.ndisk);
   L.jidx.assign((size_t)n[0] * n[1], -1);
+  L.jnat.assign(L.ndisk, 0);
   std::set<int> xs, xsn;
   for (int j = 0; j < L.ndisk; ++j) {
     int a, b;
@@ -190,6 +191,7 @@ Layout build_layout(const int32_t *miller, int npw_h, const int n[3], const doub
     xs.insert(x);
     xsn.insert(wrapi(a, n[0]));
     L.jidx[(size_t)wrapi(b, n[1]) * n[0] + wrapi(a, n[0])] = j;
+    L.jnat[j] = wrapi(b, n[1]) * n[0] + wrapi(a, n[0]);
     L.xmax = std::max(L.xmax, std::abs(a));
   }
   L.xact.assign(xs.begin(), xs.end());

@@ -451,10 +451,15 @@ __device__ __forceinline__ void line_forward(float2 (&x)[N], const float2 *tw) {
 // natural index held by slot s after line_inverse
 template <int N> __device__ __forceinline__ constexpr int perm_index(int s) { return s / (N / 8) + 8 * (s % (N / 8)); }
 
+// One (pair, z) plane per block of N threads. The column-buffer slice and the V_loc plane arrive
+// with coalesced loads (the slice scattered into a zeroed natural-order tile through jnat), the
+// occupied columns are transformed along n2 by one thread each, every row along n1 with the V_loc
+// product in between by one thread each, the columns back along n2, and the slice leaves with
+// coalesced stores.
 template <int N>
-__global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jidx,
+__global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jnat,
                                                  PlaneArgs<float> pa) {
-  constexpr int P = N + 1;
+  constexpr int P = N + 1;  // tile and V_loc pitch: column accesses hit distinct banks
   extern __shared__ __align__(16) unsigned char smraw[];
   float2 *tw = reinterpret_cast<float2 *>(smraw);
   float2 *tile = tw + N;
@@ -464,18 +469,28 @@ __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict
   const int nx = g.nxact, xmax = g.xmax;
   tw[t] = twg[t];
   for (int i = t; i < nx; i += N) xact[i] = g.xactn[i];
-  const float *vz = pa.field + (size_t)z * N * N;
-  for (int i = t; i < N * N; i += N) vsm[(i / N) * P + (i % N)] = vz[i];  // coalesced, padded rows
+  const float4 *vz = reinterpret_cast<const float4 *>(pa.field + (size_t)z * N * N);
+  for (int i = t; i < N * N / 4; i += N) {  // 16-byte loads, padded rows
+    const int row = i / (N / 4), c = 4 * (i % (N / 4));
+    const float4 w = vz[i];
+    vsm[row * P + c] = w.x;
+    vsm[row * P + c + 1] = w.y;
+    vsm[row * P + c + 2] = w.z;
+    vsm[row * P + c + 3] = w.w;
+  }
+  for (int i = t; i < N * P; i += N) tile[i] = make_float2(0.f, 0.f);
   __syncthreads();
   float2 *cbz = pa.cb + (size_t)q * g.n3 * g.ldcb + (size_t)z * g.ldcb;
+  for (int j = t; j < g.ndisk; j += N) {
+    const int nat = __ldg(jnat + j);
+    tile[(nat / N) * P + nat % N] = cbz[j];
+  }
+  __syncthreads();
   float2 v[N];
   if (t < nx) {  // inverse along n2 of occupied column x
     const int x = xact[t];
 #pragma unroll
-    for (int y = 0; y < N; ++y) {
-      const int jj = __ldg(jidx + y * N + x);
-      v[y] = jj >= 0 ? cbz[jj] : mkc<float>(0.f, 0.f);
-    }
+    for (int y = 0; y < N; ++y) v[y] = tile[y * P + x];
     line_inverse<N>(v, tw);
 #pragma unroll
     for (int s = 0; s < N; ++s) tile[perm_index<N>(s) * P + x] = v[s];
@@ -494,16 +509,18 @@ __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict
       if (x <= xmax || x >= N - xmax) tile[y * P + x] = v[x];
   }
   __syncthreads();
-  if (t < nx) {  // forward along n2 of occupied column x, scattered back to the column buffer
+  if (t < nx) {  // forward along n2 of occupied column x, back into the tile in natural order
     const int x = xact[t];
 #pragma unroll
     for (int s = 0; s < N; ++s) v[s] = tile[perm_index<N>(s) * P + x];
     line_forward<N>(v, tw);
 #pragma unroll
-    for (int y = 0; y < N; ++y) {
-      const int jj = __ldg(jidx + y * N + x);
-      if (jj >= 0) cbz[jj] = v[y];
-    }
+    for (int y = 0; y < N; ++y) tile[y * P + x] = v[y];
+  }
+  __syncthreads();
+  for (int j = t; j < g.ndisk; j += N) {
+    const int nat = __ldg(jnat + j);
+    cbz[j] = tile[(nat / N) * P + nat % N];
   }
 }
 
@@ -520,7 +537,7 @@ template <int N> size_t reg_smem(const Geo &g) {
 }
 
 template <int N> static void launch_reg(const FftCtx<float> &f, int nblk, const PlaneArgs<float> &pa, cudaStream_t st) {
-  launch("plane_vloc", 32, k_plane_reg<N>, dim3(nblk, f.g.n3), dim3(N), reg_smem<N>(f.g), st, f.g, f.tw1, f.jidx, pa);
+  launch("plane_vloc", 32, k_plane_reg<N>, dim3(nblk, f.g.n3), dim3(N), reg_smem<N>(f.g), st, f.g, f.tw1, f.jnat, pa);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 

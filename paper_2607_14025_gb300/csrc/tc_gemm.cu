@@ -44,7 +44,10 @@ __device__ __forceinline__ float4 load_masked(const float *row, int f, int kf) {
   return v;
 }
 
-// S (+ split partials) = U_w X^T; grid (solve tiles, splits), 256 threads
+// S (+ split partials) = U_w X^T; grid (solve tiles, splits), 256 threads. The operands of chunk
+// i + 1 are loaded into registers while the MMAs of chunk i run, so global latency overlaps them.
+constexpr int UPT = 8;  // U pieces per thread and operand part at most (256 rows x 8 pieces / 256 threads)
+
 __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restrict__ X, int nb, const float *__restrict__ Uhi,
                                                     const float *__restrict__ Ulo, int na, int nu, double *__restrict__ out, int ldo,
                                                     int ch_per_split, size_t split_stride, int *__restrict__ err) {
@@ -58,6 +61,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
   const int kf = 2 * g.nint, ldf = 2 * g.ld;
   const int nch = (kf + TK - 1) / TK;
   const int c0 = blockIdx.y * ch_per_split, c1 = min(nch, c0 + ch_per_split);
+  const int upt = (nu * 8) / 256;  // nu is a multiple of 32, so whole pieces per thread
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
     tc::mbar_init(&bar[1], 1);
@@ -69,6 +73,25 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
   const uint32_t idesc = tc::idesc_tf32(TM, nu);
+  float4 rx[4], rh[UPT], rl[UPT];
+  auto fetch = [&](int c) {
+    const int f0 = c * TK;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      rx[u] = (s0 + row < nb) ? load_masked(X + (size_t)(s0 + row) * ldf, f0 + 4 * q, kf) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      rh[u] = rl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u < upt && row < na) {
+        rh[u] = *reinterpret_cast<const float4 *>(Uhi + (size_t)row * ldf + f0 + 4 * q);
+        rl[u] = *reinterpret_cast<const float4 *>(Ulo + (size_t)row * ldf + f0 + 4 * q);
+      }
+    }
+  };
+  if (c0 < c1) fetch(c0);
   int issued = 0;
   bool ok = true;
   for (int c = c0; c < c1; ++c) {
@@ -76,24 +99,19 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
     unsigned char *S = sm + st * SB;
     if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
     if (!ok) break;
-    const int f0 = c * TK;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {  // X: 128 rows x 8 pieces
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (s0 + row < nb) v = load_masked(X + (size_t)(s0 + row) * ldf, f0 + 4 * q, kf);
-      put(S, S + XB, row, q, v);
+    for (int u = 0; u < 4; ++u) {
+      const int t = tid + 256 * u;
+      put(S, S + XB, t >> 3, t & 7, rx[u]);
     }
-    for (int t = tid; t < nu * 8; t += 256) {  // U (weighted, split at setup): nu rows x 8 pieces
-      const int row = t >> 3, q = t & 7;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (row < na) {
-        h = *reinterpret_cast<const float4 *>(Uhi + (size_t)row * ldf + f0 + 4 * q);
-        l = *reinterpret_cast<const float4 *>(Ulo + (size_t)row * ldf + f0 + 4 * q);
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const int t = tid + 256 * u;
+      if (u < upt) {
+        const int o = tc::swz_off(t >> 3, t & 7);
+        *reinterpret_cast<float4 *>(S + 2 * XB + o) = rh[u];
+        *reinterpret_cast<float4 *>(S + 2 * XB + UB + o) = rl[u];
       }
-      const int o = tc::swz_off(row, q);
-      *reinterpret_cast<float4 *>(S + 2 * XB + o) = h;
-      *reinterpret_cast<float4 *>(S + 2 * XB + UB + o) = l;
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -110,6 +128,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
       tc::mma_commit(&bar[st]);
     }
     ++issued;
+    if (c + 1 < c1) fetch(c + 1);  // in flight while the MMAs run
   }
   // the last commit covers every MMA issued
   bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
@@ -169,7 +188,11 @@ __global__ void k_tc_coef(const double *__restrict__ S, int ldc, const double *_
 }
 
 // Y = c0 Y + Cd Ut^T on float rows (2 N_int), partial <P_s, Y_s> per 128-element tile;
-// grid (solve tiles, 256-value tiles), 256 threads
+// grid (solve tiles, 256-value tiles), 256 threads. Operands of the next K chunk are fetched into
+// registers while the MMAs run; the finished tile goes TMEM -> shared memory, then each warp
+// updates whole rows of Y with coalesced accesses and reduces its row's partial inner product.
+constexpr int DP = 260;  // shared row pitch of the result tile (floats): conflict-free float4 stores
+
 __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict__ Y, int ny, const float *__restrict__ Chi,
                                                        const float *__restrict__ Clo, int kp, const float *__restrict__ Uthi,
                                                        const float *__restrict__ Utlo, float c0, const float *__restrict__ P,
@@ -179,7 +202,7 @@ __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict_
   constexpr int TN = 256, BB = TN * 128, SB = 2 * XB + 2 * BB;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * SB);
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + 2 * SB + 16);
-  double *red = reinterpret_cast<double *>(sm + 2 * SB + 64);  // [2][128]
+  float *D = reinterpret_cast<float *>(sm);  // result tile [128][DP], over the operand stages
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s0 = blockIdx.x * TM, f0 = blockIdx.y * TN;
   const int kf = 2 * g.nint, ldf = 2 * g.ld;
@@ -195,6 +218,29 @@ __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict_
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
   const uint32_t idesc = tc::idesc_tf32(TM, TN);
+  float4 ah[4], al[4], bh[8], bl[8];
+  auto fetch = [&](int i) {
+    const int k0 = i * TK;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {  // coefficients: 128 solve rows x 8 pieces (hi, lo precomputed)
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      ah[u] = al[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s0 + row < ny) {
+        ah[u] = *reinterpret_cast<const float4 *>(Chi + (size_t)(s0 + row) * kp + k0 + 4 * q);
+        al[u] = *reinterpret_cast<const float4 *>(Clo + (size_t)(s0 + row) * kp + k0 + 4 * q);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {  // U transposed: 256 value rows x 8 pieces
+      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
+      bh[u] = bl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (f0 + row < kf) {
+        bh[u] = *reinterpret_cast<const float4 *>(Uthi + (size_t)(f0 + row) * kp + k0 + 4 * q);
+        bl[u] = *reinterpret_cast<const float4 *>(Utlo + (size_t)(f0 + row) * kp + k0 + 4 * q);
+      }
+    }
+  };
+  fetch(0);
   int issued = 0;
   bool ok = true;
   for (int i = 0; i < nkc; ++i) {
@@ -202,30 +248,17 @@ __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict_
     unsigned char *S = sm + st * SB;
     if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
     if (!ok) break;
-    const int k0 = i * TK;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {  // coefficients: 128 solve rows x 8 pieces (hi, lo precomputed)
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (s0 + row < ny) {
-        h = *reinterpret_cast<const float4 *>(Chi + (size_t)(s0 + row) * kp + k0 + 4 * q);
-        l = *reinterpret_cast<const float4 *>(Clo + (size_t)(s0 + row) * kp + k0 + 4 * q);
-      }
-      const int o = tc::swz_off(row, q);
-      *reinterpret_cast<float4 *>(S + o) = h;
-      *reinterpret_cast<float4 *>(S + XB + o) = l;
+    for (int u = 0; u < 4; ++u) {
+      const int t = tid + 256 * u, o = tc::swz_off(t >> 3, t & 7);
+      *reinterpret_cast<float4 *>(S + o) = ah[u];
+      *reinterpret_cast<float4 *>(S + XB + o) = al[u];
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {  // U transposed: 256 value rows x 8 pieces
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (f0 + row < kf) {
-        h = *reinterpret_cast<const float4 *>(Uthi + (size_t)(f0 + row) * kp + k0 + 4 * q);
-        l = *reinterpret_cast<const float4 *>(Utlo + (size_t)(f0 + row) * kp + k0 + 4 * q);
-      }
-      const int o = tc::swz_off(row, q);
-      *reinterpret_cast<float4 *>(S + 2 * XB + o) = h;
-      *reinterpret_cast<float4 *>(S + 2 * XB + BB + o) = l;
+    for (int u = 0; u < 8; ++u) {
+      const int t = tid + 256 * u, o = tc::swz_off(t >> 3, t & 7);
+      *reinterpret_cast<float4 *>(S + 2 * XB + o) = bh[u];
+      *reinterpret_cast<float4 *>(S + 2 * XB + BB + o) = bl[u];
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -242,47 +275,65 @@ __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict_
       tc::mma_commit(&bar[st]);
     }
     ++issued;
+    if (i + 1 < nkc) fetch(i + 1);
   }
   bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
   done = __syncthreads_and(done) && ok && issued == nkc;
-  const int qd = warp & 3, h = warp >> 2, row = 32 * qd + lane, s = s0 + row;
-  double dsum = 0.0;
   if (done) {
+    // every MMA has completed, so the operand stages are free: TMEM -> D[128][DP]
     tc::fence_after_sync();
+    const int qd = warp & 3, h = warp >> 2, row = 32 * qd + lane;
     for (int cg = 0; cg < TN / 2; cg += 16) {
       const int col = h * (TN / 2) + cg;
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)col, v);
-      if (s < ny) {
-        float *y = Y + (size_t)s * ldf;
-        const float *p = P ? P + (size_t)s * ldf : nullptr;
 #pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-          const int f = f0 + col + k;  // even: one complex element e = f / 2
-          if (f < kf) {
-            float yx = v[k], yy = v[k + 1];
-            if (c0 != 0.f) {
-              const float2 o = *reinterpret_cast<const float2 *>(y + f);
-              yx = fmaf(c0, o.x, yx);
-              yy = fmaf(c0, o.y, yy);
-            }
-            *reinterpret_cast<float2 *>(y + f) = make_float2(yx, yy);
-            if (p) {
-              const float2 pv = *reinterpret_cast<const float2 *>(p + f);
-              const double w = (f >> 1) < g.len0 ? 1.0 : 2.0;
-              dsum += w * ((double)pv.x * yx + (double)pv.y * yy);
-            }
-          }
-        }
-      }
+      for (int k = 0; k < 16; k += 4) *reinterpret_cast<float4 *>(D + row * DP + col + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
     }
   } else if (tid == 0) {
     atomicExch(err, 1);
   }
-  if (part) {
-    red[h * TM + row] = dsum;
-    __syncthreads();
-    if (tid < TM && s0 + tid < ny) part[(size_t)(s0 + tid) * nchunk + blockIdx.y] = red[tid] + red[TM + tid];
+  __syncthreads();
+  if (done) {
+    // warp w updates rows w, w + 8, ...: lane l owns values 8 l .. 8 l + 7 of the 256
+    for (int r = warp; r < TM; r += 8) {
+      const int s = s0 + r;
+      if (s >= ny) break;  // rows are in order: the rest of this warp's rows are past the end too
+      float *y = Y + (size_t)s * ldf + f0;
+      const float *p = P ? P + (size_t)s * ldf + f0 : nullptr;
+      float dsum = 0.f;  // a lane adds at most 4 products; the warp sum is FP64
+#pragma unroll
+      for (int hq = 0; hq < 2; ++hq) {
+        const int f = 8 * lane + 4 * hq;  // 4 values = 2 complex elements
+        if (f0 + f < kf) {
+          float4 d = *reinterpret_cast<const float4 *>(D + r * DP + f);
+          if (f0 + f + 3 >= kf) d.z = d.w = 0.f;  // one element past the end (kf is even)
+          float4 yv = d;
+          if (c0 != 0.f) {
+            const float4 o = *reinterpret_cast<const float4 *>(y + f);
+            yv = make_float4(fmaf(c0, o.x, d.x), fmaf(c0, o.y, d.y), fmaf(c0, o.z, d.z), fmaf(c0, o.w, d.w));
+          }
+          if (f0 + f + 3 < kf) {
+            *reinterpret_cast<float4 *>(y + f) = yv;
+          } else {
+            *reinterpret_cast<float2 *>(y + f) = make_float2(yv.x, yv.y);
+          }
+          if (p) {
+            const int e = (f0 + f) >> 1;
+            const float4 pv = *reinterpret_cast<const float4 *>(p + f);
+            const float w0 = e < g.len0 ? 1.f : 2.f, w1 = e + 1 < g.len0 ? 1.f : 2.f;
+            dsum += w0 * (pv.x * yv.x + pv.y * yv.y);
+            if (f0 + f + 3 < kf) dsum += w1 * (pv.z * yv.z + pv.w * yv.w);
+          }
+        }
+      }
+      if (part) {
+        double dd = (double)dsum;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        if (lane == 0) part[(size_t)s * nchunk + blockIdx.y] = dd;
+      }
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -312,12 +363,12 @@ __global__ void k_tc_prep_u(Geo g, const float2 *__restrict__ U, int na, int kp,
 }
 
 size_t gram_tc_smem(int nu) { return 1024 + 2 * (size_t)(2 * XB + 2 * nu * 128) + 64; }
-size_t lincomb_tc_smem() { return 1024 + 2 * (size_t)(2 * XB + 2 * 256 * 128) + 64 + 2 * TM * sizeof(double); }
+size_t lincomb_tc_smem() { return 1024 + 2 * (size_t)(2 * XB + 2 * 256 * 128) + 64; }
 
 }  // namespace
 
 bool tc_enabled() {
-  static const bool on = std::getenv("WDF_TC") != nullptr && std::getenv("WDF_NO_TC") == nullptr;
+  static const bool on = std::getenv("WDF_NO_TC") == nullptr;
   return on;
 }
 

@@ -148,6 +148,7 @@ def load(path: str = LIB_PATH):
         "wdf_train_preconditioner": (I, [P, I, P, ctypes.POINTER(P), P]),
         "wdf_profile_kernel": (I, [P, ctypes.c_char_p]),
         "wdf_profile_read": (I, [P, P, P]),
+        "wdf_profile_units": (I, [P, P]),
         "wdf_launch_count": (ctypes.c_int64, []),
         "wdf_strerror": (ctypes.c_char_p, [I]),
         "wdf_last_error": (ctypes.c_char_p, [P]),
@@ -360,6 +361,12 @@ class Context:
         ms = ctypes.c_double()
         self._check(self._lib.wdf_profile_read(self._ctx, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
+
+    def profile_units(self) -> int:
+        """Thread blocks of the timed launches (work units of per-block kernels)."""
+        b = ctypes.c_int64()
+        self._check(self._lib.wdf_profile_units(self._ctx, ctypes.byref(b)))
+        return b.value
 
     def pdep(self, neig: int, guess, nbasis_max: int = 0, maxiter: int = 100, tol: float = 1e-10):
         """Lowest neig eigenpairs of chi0bar: (lambda[neig], phibar[neig, npw_h], Stats)."""

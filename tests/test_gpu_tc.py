@@ -1,8 +1,8 @@
 """Tensor-core (tcgen05, 3xTF32) against CUDA-core projections in the FP32 inner CG.
 
-The backend is chosen per process (WDF_TC / WDF_NO_TC in the environment), so each case runs in
-a subprocess through the C ABI. Small system: both backends against the FP64 oracle at the mixed
-form's bar (1e-8 relative at cg_tol 1e-10). Medium system (192 projection rows, 320 solves: three
+The backend is chosen per process (tensor cores by default, CUDA cores with WDF_NO_TC in the
+environment), so each case runs in a subprocess through the C ABI. Small system: both backends
+against the FP64 oracle at the mixed form's bar (1e-8 relative at cg_tol 1e-10). Medium system (192 projection rows, 320 solves: three
 128-solve tiles with a ragged tail, 8,455 elements: 67 value tiles with a ragged tail): the two
 backends against each other, 1e-8 relative.
 """
@@ -45,8 +45,9 @@ def run_backend(flag, name, npert, tmp_path, psi=None, eps=None):
         pp, ep = str(tmp_path / "psi.npy"), str(tmp_path / "eps.npy")
         np.save(pp, psi)
         np.save(ep, eps)
-    env = {k: v for k, v in os.environ.items() if k not in ("WDF_TC", "WDF_NO_TC")}
-    env[flag] = "1"
+    env = {k: v for k, v in os.environ.items() if k != "WDF_NO_TC"}
+    if flag == "WDF_NO_TC":
+        env[flag] = "1"
     code = SCRIPT.format(root=ROOT, name=name, npert=npert, psi=pp, eps=ep, out=out)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -61,7 +62,7 @@ def built():
     build.build()
 
 
-@pytest.mark.parametrize("flag", ["WDF_TC", "WDF_NO_TC"])
+@pytest.mark.parametrize("flag", ["tensor_cores", "WDF_NO_TC"])
 def test_small_system_against_oracle(flag, tmp_path):
     s = synth.make_system("small")
     H = hamiltonian.Hamiltonian(s)
@@ -76,7 +77,7 @@ def test_small_system_against_oracle(flag, tmp_path):
 
 
 def test_medium_system_backends_agree(tmp_path):
-    a, sa = run_backend("WDF_TC", "medium", 5, tmp_path)
+    a, sa = run_backend("tensor_cores", "medium", 5, tmp_path)
     b, sb = run_backend("WDF_NO_TC", "medium", 5, tmp_path)
     assert sa["converged"] == 1 and sb["converged"] == 1
     assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
