@@ -83,3 +83,23 @@ def dense_eigs(chi_real: np.ndarray, neig: int):
     """Lowest ``neig`` eigenvalues of an explicit real symmetric chi0bar matrix."""
     w = np.linalg.eigvalsh(chi_real)
     return w[:neig]
+
+
+def chibar_lowrank(lam: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """chi-bar of Eq. (5) without Xi: sum_a q_a lam_a / (1 - lam_a) q_a^T (real coordinates).
+
+    q: (neig, d) orthonormal rows (the PDEP eigenvectors in real coordinates). With orthonormal
+    plane-wave coefficient vectors the 1/Omega of Eq. (5) is absorbed: it belongs to the paper's
+    real-space normalisation of the eigenpotentials. RPA: chi = chi0 + chi0 chi, so with every
+    eigenpair this equals (1 - chi0)^-1 chi0.
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    return (q.T * (lam / (1.0 - lam))[None, :]) @ q
+
+
+def wp_apply(lam: np.ndarray, phibar_half: np.ndarray, vhalf_half: np.ndarray, x_half: np.ndarray) -> np.ndarray:
+    """W_p x = v^1/2 chi-bar v^1/2 x for half-sphere rows x, chi-bar from chibar_lowrank."""
+    q = basis.half_to_real(np.atleast_2d(phibar_half))
+    y = basis.half_to_real(vhalf_half[None, :] * np.atleast_2d(x_half))
+    z = (chibar_lowrank(lam, q) @ y.T).T
+    return vhalf_half[None, :] * basis.real_to_half(z)

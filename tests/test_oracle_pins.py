@@ -309,3 +309,32 @@ def test_medium_system_has_the_required_gap():
     H = hamiltonian.Hamiltonian(s)
     w, _ = H.ground_state(s.nocc + 1, tol=1e-8)
     assert w[s.nocc] - w[s.nocc - 1] > 0.1
+
+
+def test_lowrank_chibar_with_every_eigenpair_is_the_rpa_inverse(tiny):
+    # Eq. (5) without Xi: with all eigenpairs of chi0bar the low-rank sum is exact, and RPA
+    # (chi = chi0 + chi0 chi) fixes it as (1 - chi0)^-1 chi0
+    s, H, eps_all, psi_all, R = tiny
+    chi0 = dfpt.adler_wiser_chi0bar(H, eps_all, psi_all, s.nocc)
+    w, V = np.linalg.eigh(chi0)
+    full = pdep.chibar_lowrank(w, V.T)
+    rpa = np.linalg.solve(np.eye(len(w)) - chi0, chi0)
+    assert np.abs(full - rpa).max() <= 1e-12 * np.abs(rpa).max()
+    # W_p = v^1/2 chi v^1/2 through the half-sphere interface, against the matrix (G != 0 block)
+    m = s.npw_h
+    vh = R.vhalf[:m]
+    x = synth.make_perturbations(s, 3, 4)
+    phib = basis.real_to_half(np.concatenate([np.zeros((len(w), 1)), V.T], axis=1))
+    got = basis.half_to_real(pdep.wp_apply(w, phib, vh, x))[:, 1:]
+    vreal = np.concatenate([vh[1:], vh[1:]])  # real coordinates: sqrt(2) Re c_G, then sqrt(2) Im c_G
+    want = ((vreal[:, None] * rpa * vreal[None, :]) @ basis.half_to_real(x)[:, 1:].T).T
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_planted_wrong_screening_factor_is_caught(monkeypatch, tiny):
+    s, H, eps_all, psi_all, R = tiny
+    chi0 = dfpt.adler_wiser_chi0bar(H, eps_all, psi_all, s.nocc)
+    w, V = np.linalg.eigh(chi0)
+    rpa = np.linalg.solve(np.eye(len(w)) - chi0, chi0)
+    bad = (V * w[None, :]) @ V.T  # lambda instead of lambda / (1 - lambda): chi0 itself
+    assert np.abs(bad - rpa).max() > 1e-2 * np.abs(rpa).max()
