@@ -380,6 +380,67 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_batching(args):
+    """The batching workload: 16 seeded systems of uneven size (grids 32^3-80^3, 10-148 occupied
+    orbitals) with their perturbation blocks in one wdf_apply_chi0_multi call per step, against
+    the same applies one system after another. Host buffers: the timings are end to end."""
+    import torch
+
+    from paper_2607_14025_gb300 import build as wbuild
+    from paper_2607_14025_gb300 import wdf
+
+    torch.cuda.set_device(0)
+    wbuild.build()
+    specs = synth.batch_family(args.batch_systems, seed=0)
+    t0 = time.perf_counter()
+    systems = [synth.make_system(sp) for sp in specs]
+    ctxs = [wdf.Context(s, precision=args.precision, cg_tol=1e-8) for s in systems]
+    t_setup = time.perf_counter() - t0
+    phis = [synth.make_perturbations(s, args.batch_npert, 500 + k) for k, s in enumerate(systems)]
+    nsolve = sum(args.batch_npert * s.nocc for s in systems)
+
+    def multi():
+        try:
+            return wdf.apply_chi0_multi(ctxs, phis)[1]
+        except wdf.NotConverged as e:
+            return e.result[1]
+
+    for _ in range(args.warmup):
+        multi()
+    clk = Clocks(0)
+    clk.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = multi()
+    ms_multi = 1e3 * (time.perf_counter() - t0) / args.steps
+    clocks = clk.stop()
+    t0 = time.perf_counter()
+    for c, p in zip(ctxs, phis):
+        try:
+            c.apply_chi0(p)
+        except wdf.NotConverged:
+            pass
+    ms_seq = 1e3 * (time.perf_counter() - t0)
+    for c in ctxs:
+        c.close()
+    value = nsolve / (ms_multi * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_multi, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "mixed_df": "f32+df64+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": f"batching: {len(specs)} systems, grids " + ",".join(str(sp.grid[0]) for sp in specs)
+                               + f"; {args.batch_npert} perturbations each; {nsolve} solves per step",
+                   "precision": args.precision, "cg_tol": 1e-8, "timing": "host clock around the multi-system call (host buffers)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": sum(p.nbytes for p in phis),
+                "d2h_bytes_per_step": sum(p.nbytes for p in phis)},
+        "sequential": {"value": nsolve / (ms_seq * 1e-3), "ms_per_step": ms_seq},
+        "multi_over_sequential": ms_seq / ms_multi,
+        "cg_iters_per_solve": sum(x.cg_iters for x in st) / max(1, sum(x.nsolve for x in st)),
+        "max_residual": max(x.max_residual for x in st), "setup_s": t_setup, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +457,10 @@ def main():
                     help="learned: train the MLP preconditioner on other seeds of the family first (not timed)")
     ap.add_argument("--no-learned", dest="with_learned", action="store_false",
                     help="skip the extra timing of the learned preconditioner after the TPA headline")
+    ap.add_argument("--workload", choices=["medium", "batching"], default="medium",
+                    help="batching: the uneven multi-system workload (its own line; medium is the headline)")
+    ap.add_argument("--batch-systems", type=int, default=16)
+    ap.add_argument("--batch-npert", type=int, default=64)
     ap.add_argument("--train-systems", type=int, default=4)
     ap.add_argument("--train-npert", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=600)
@@ -405,6 +470,8 @@ def main():
     NEIG = min(NEIG, NPERT)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batching":
+        run_batching(args)
     else:
         run_gpu(args)
 

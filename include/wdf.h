@@ -133,6 +133,22 @@ void wdf_default_options(wdf_options *opt);
  * did not converge: the context is still created and usable), WDF_ENAN. */
 int wdf_setup_hamiltonian(wdf_ctx **out, const wdf_system *sys, const wdf_options *opt);
 
+/* The canonical Gamma half sphere of {G : |G|^2 <= ecut} (ecut in bohr^-2) for the cell with
+ * lattice vectors as rows: Miller triples with n3 > 0, or n3 = 0 and n2 > 0, or n3 = n2 = 0 and
+ * n1 >= 0, ordered by |G|^2 (shells equal to 1e-9 ecut count as one) and then by (n1, n2, n3);
+ * G = 0 first. This is the order wdf_system.miller expects. Host only (no GPU needed).
+ * miller: NULL to query the count, else room for *npw_h triples. *npw_h: in, the room; out,
+ * the count. Errors: WDF_EINVAL (singular cell, ecut <= 0, too little room). */
+int wdf_half_sphere(const double cell[9], double ecut, int32_t *miller, int *npw_h);
+
+/* Copy the context's Miller triples [npw_h][3] (host). */
+int wdf_get_gvectors(const wdf_ctx *ctx, int32_t *miller);
+
+/* Make a failed context usable again when the failure did not leave the device faulted (a
+ * refused launch, an expired bounded wait): clears the error and returns WDF_OK; WDF_ESTATE
+ * when the device reports a fault (then only wdf_destroy remains). */
+int wdf_reset_error(wdf_ctx *ctx);
+
 /* Release the context and all its device memory. NULL is ignored. */
 void wdf_destroy(wdf_ctx *ctx);
 
@@ -165,6 +181,26 @@ int wdf_sternheimer(wdf_ctx *ctx, int nsolve, const int32_t *vidx, const double 
 int wdf_apply_chi0(wdf_ctx *ctx, int npert, const double *phi, double *out, double *drho, int mem,
                    wdf_stats *st);
 
+/* W_p x for nvec vectors from PDEP eigenpairs: the low-rank form of Eq. (5) without the
+ * long-range term Xi, W_p = v^1/2 chibar v^1/2 with chibar = sum_a phibar_a lambda_a / (1 - lambda_a)
+ * phibar_a^dagger (phibar orthonormal coefficient vectors, as wdf_pdep_davidson returns them; the
+ * 1/Omega of Eq. (5) belongs to the paper's real-space normalisation of the eigenpotentials).
+ * lambda: [neig] host, each < 1. phibar: [neig][npw_h]; in, out: [nvec][npw_h] complex, host or
+ * device per mem; out may alias in. Errors: WDF_EINVAL. */
+int wdf_apply_wp(wdf_ctx *ctx, int neig, const double *lambda, const double *phibar, int nvec, const double *in,
+                 double *out, int mem);
+
+/* chi0bar for several systems at once (batching form): out[k] = chi0bar phi[k] for context
+ * ctx[k] and npert[k] perturbations, exactly as wdf_apply_chi0 would compute it. The systems run
+ * concurrently, one host thread per system, each on its context's stream (a context on the
+ * legacy default stream gets a private stream for the call), so that systems too small to fill
+ * the GPU overlap. Contexts must be distinct and on one GPU; phi[k], out[k] host or device per
+ * mem. st: NULL or an array of nsys statistics. Returns WDF_OK, the first error of a system, or
+ * WDF_ENOCONV when every system finished but one did not converge; wdf_last_error(NULL) names
+ * the failing system. */
+int wdf_apply_chi0_multi(int nsys, wdf_ctx *const *ctx, const int *npert, const double *const *phi,
+                         double *const *out, int mem, wdf_stats *st);
+
 /* PDEP: the neig algebraically lowest eigenpairs of chi0bar (Eq. (5): lambda_a, phibar_a) by
  * block Davidson. Start block: the nguess vectors of guess (G = 0 entries ignored), at least
  * neig of them; expansion by the residuals of the unconverged Ritz pairs, two-pass classical
@@ -176,6 +212,12 @@ int wdf_apply_chi0(wdf_ctx *ctx, int npert, const double *phi, double *out, doub
 int wdf_pdep_davidson(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, double tol,
                       int nguess, const double *guess, double *lambda, double *phibar, int mem,
                       wdf_stats *st);
+
+/* wdf_pdep_davidson from neig start vectors drawn by the library: Gaussian real and imaginary
+ * parts from splitmix64(seed) (Steele, Lea, Flood 2014) with Box-Muller, G = 0 removed, each
+ * scaled to unit norm. lambda host; phibar host or device per mem. */
+int wdf_pdep_davidson_seeded(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, double tol, uint64_t seed,
+                             double *lambda, double *phibar, int mem, wdf_stats *st);
 
 /* Bytes of the device array behind wdf_apply_hamiltonian_noalloc: 64 MiB, present on every GPU
  * that loads the library for the life of the process. */

@@ -4,7 +4,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
+#include <thread>
 #include <algorithm>
 
 #include "engine.cuh"
@@ -18,6 +21,18 @@ const char *last_global_error() { return g_last_error.c_str(); }
 
 thread_local Profiler *t_prof = nullptr;
 std::atomic<long long> g_launches{0};
+
+void raise_smem_limit_raw(const void *func, size_t bytes) {
+  static std::mutex m;
+  static std::map<std::pair<int, const void *>, size_t> cur;
+  int dev = 0;
+  WDF_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(m);
+  size_t &c = cur[{dev, func}];
+  if (bytes <= c) return;
+  WDF_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  c = bytes;
+}
 
 void prof_record(cudaStream_t st) {
   Profiler *p = t_prof;
@@ -154,6 +169,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   c->nproj = sys->nproj;
   c->nocc = sys->nocc;
   c->lay = build_layout(sys->miller, sys->npw_h, sys->n, c->bvec);
+  c->miller.assign(sys->miller, sys->miller + 3 * (size_t)sys->npw_h);
   const Layout &L = c->lay;
   if (2 * L.nint - L.len0 <= c->nocc) throw ApiFailure(WDF_EINVAL, "more occupied orbitals than plane waves");
   c->ngrid = (size_t)sys->n[0] * sys->n[1] * sys->n[2];
@@ -405,7 +421,8 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->t_twdf,    &c->vlocdf,    &c->Udf,     &c->psirdf,   &c->dfa,     &c->dfb,
                   &c->xpdf,      &c->dvgriddf,  &c->accgriddf, &c->cb2df,  &c->drdf,    &c->oudf, &c->chol,
                   &c->ml64,      &c->ml32,      &c->mlw64,   &c->krow,     &c->rr_ref,  &c->it_ref,  &c->nfb,
-                  &c->mlsums,    &c->mlwraw,    &c->tcU,     &c->tcUt,     &c->tcC,     &c->tcerr};
+                  &c->mlsums,    &c->mlwraw,    &c->tcU,     &c->tcUt,     &c->tcC,     &c->tcerr,
+                  &c->wp_phi,    &c->wp_x,      &c->wp_y,    &c->wp_vx,    &c->wp_S,    &c->wp_coef};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {
@@ -486,6 +503,92 @@ int wdf_apply_chi0(wdf_ctx *c, int npert, const double *phi, double *out, double
     fill_stats(st, ss, (long long)npert * c->nocc, npert, tm.ms());
     return ss.converged ? WDF_OK : WDF_ENOCONV;
   });
+}
+
+int wdf_apply_wp(wdf_ctx *c, int neig, const double *lambda, const double *phibar, int nvec, const double *in, double *out, int mem) {
+  if (!c) return WDF_EINVAL;
+  return guarded(c, [&] {
+    check_mem(mem);
+    if (neig < 1 || nvec < 0 || !lambda || !phibar || (nvec > 0 && (!in || !out))) throw ApiFailure(WDF_EINVAL, "bad arguments");
+    std::vector<double> coef(neig);
+    for (int a = 0; a < neig; ++a) {
+      if (!(lambda[a] < 1.0)) throw ApiFailure(WDF_EINVAL, "an eigenvalue lambda >= 1 has no screening factor lambda / (1 - lambda)");
+      coef[a] = lambda[a] / (1.0 - lambda[a]);
+    }
+    if (nvec == 0) return WDF_OK;
+    cplx<double> *P = read_in(c, c->ext_in, c->wp_phi, phibar, neig, mem);
+    cplx<double> *X = read_in(c, c->ext_out2, c->wp_x, in, nvec, mem);
+    c->wp_coef.ensure(sizeof(double) * neig);
+    WDF_CUDA_TRY(cudaMemcpyAsync(c->wp_coef.p, coef.data(), sizeof(double) * neig, cudaMemcpyHostToDevice, c->st));
+    c->wp_y.ensure(sizeof(cplx<double>) * (size_t)nvec * c->geo.ld);
+    wp_apply_internal(c, P, c->wp_coef.as<double>(), neig, X, nvec, c->wp_y.as<cplx<double>>());
+    write_out(c, c->ext_out, c->wp_y.as<cplx<double>>(), nvec, out, mem);
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    return WDF_OK;
+  });
+}
+
+int wdf_apply_chi0_multi(int nsys, wdf_ctx *const *ctx, const int *npert, const double *const *phi, double *const *out, int mem,
+                         wdf_stats *st) {
+  if (nsys < 1 || !ctx || !npert || !phi || !out) {
+    set_error(WDF_EINVAL, "bad nsys or NULL array");
+    return WDF_EINVAL;
+  }
+  for (int k = 0; k < nsys; ++k) {
+    if (!ctx[k] || ctx[k]->device != ctx[0]->device) {
+      set_error(WDF_EINVAL, "contexts must be non-NULL and on one GPU");
+      return WDF_EINVAL;
+    }
+    for (int j = 0; j < k; ++j)
+      if (ctx[j] == ctx[k]) {
+        set_error(WDF_EINVAL, "a context appears twice");
+        return WDF_EINVAL;
+      }
+  }
+  // one host thread per system; a context on the legacy default stream gets a private stream
+  // for the call so that the systems' kernels can overlap
+  std::vector<int> rc(nsys, WDF_OK);
+  std::vector<std::string> msg(nsys);
+  auto work = [&](int k) {
+    wdf_ctx *c = ctx[k];
+    cudaStream_t saved = c->st, own = nullptr;
+    if (!saved) {
+      if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc[k] = WDF_ECUDA;
+        msg[k] = "stream creation failed";
+        return;
+      }
+      c->st = own;
+    }
+    rc[k] = wdf_apply_chi0(c, npert[k], phi[k], out[k], nullptr, mem, st ? &st[k] : nullptr);
+    if (rc[k] != WDF_OK) msg[k] = c->err;
+    if (own) {
+      (void)cudaStreamSynchronize(own);
+      (void)cudaStreamDestroy(own);
+      c->st = saved;
+    }
+  };
+  try {
+    std::vector<std::thread> th;
+    th.reserve(nsys);
+    for (int k = 1; k < nsys; ++k) th.emplace_back(work, k);
+    work(0);
+    for (auto &t : th) t.join();
+  } catch (const std::exception &) {
+    set_error(WDF_EINVAL, "could not start the host threads");
+    return WDF_EINVAL;
+  }
+  // the worst status wins: any error before not-converged
+  int worst = WDF_OK;
+  for (int k = 0; k < nsys; ++k) {
+    if (rc[k] != WDF_OK && rc[k] != WDF_ENOCONV) {
+      set_error(rc[k], "system " + std::to_string(k) + ": " + msg[k]);
+      return rc[k];
+    }
+    if (rc[k] == WDF_ENOCONV) worst = WDF_ENOCONV;
+  }
+  return worst;
 }
 
 int wdf_pdep_davidson(wdf_ctx *c, int neig, int nbasis_max, int maxiter, double tol, int nguess, const double *guess,
@@ -600,6 +703,26 @@ double unit_open(uint64_t x) { return ((double)(x >> 11) + 0.5) * (1.0 / 9007199
 double normal_at(uint64_t seed, uint64_t k) {
   const double u1 = unit_open(splitmix64(seed, 2 * k)), u2 = unit_open(splitmix64(seed, 2 * k + 1));
   return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+// n vectors of np half-sphere coefficients: Gaussian real and imaginary parts from
+// splitmix64(seed) (entry pair k of vector p uses outputs 2 (p np + i), +1), G = 0 set to zero,
+// each scaled to unit Gamma norm a0^2 + 2 sum_{G != 0} |a_G|^2
+std::vector<double> gaussian_vectors(uint64_t seed, int n, int np) {
+  std::vector<double> v(2 * (size_t)n * np);
+  for (int p = 0; p < n; ++p) {
+    double nrm = 0.0;
+    for (int i = 0; i < np; ++i) {
+      double *c2 = &v[2 * ((size_t)p * np + i)];
+      const uint64_t idx = 2 * ((uint64_t)p * np + i);
+      c2[0] = i == 0 ? 0.0 : normal_at(seed, idx);
+      c2[1] = i == 0 ? 0.0 : normal_at(seed, idx + 1);
+      nrm += 2.0 * (c2[0] * c2[0] + c2[1] * c2[1]);
+    }
+    const double sc = nrm > 0 ? 1.0 / std::sqrt(nrm) : 0.0;
+    for (int i = 0; i < 2 * np; ++i) v[2 * (size_t)p * np + i] *= sc;
+  }
+  return v;
 }
 
 template <class F> int mguard(wdf_model *m, F &&body) {
@@ -967,21 +1090,7 @@ int wdf_train_preconditioner(wdf_ctx *const *ctx, int n, const wdf_train_opts *o
   if (rc != WDF_OK) return rc;
   for (int k = 0; k < n && rc == WDF_OK; ++k) {
     // perturbations: Gaussian coefficients from splitmix64(seed + k + 1), G = 0 removed, unit norm
-    const int np = ctx[k]->npw_h;
-    std::vector<double> phi(2 * (size_t)o.npert * np);
-    const uint64_t seed = o.seed + (uint64_t)k + 1;
-    for (int p = 0; p < o.npert; ++p) {
-      double nrm = 0.0;
-      for (int i = 0; i < np; ++i) {
-        double *c2 = &phi[2 * ((size_t)p * np + i)];
-        const uint64_t idx = 2 * ((uint64_t)p * np + i);
-        c2[0] = i == 0 ? 0.0 : normal_at(seed, idx);
-        c2[1] = i == 0 ? 0.0 : normal_at(seed, idx + 1);
-        nrm += 2.0 * (c2[0] * c2[0] + c2[1] * c2[1]);
-      }
-      const double s = 1.0 / std::sqrt(nrm);
-      for (int i = 0; i < 2 * np; ++i) phi[2 * (size_t)p * np + i] *= s;
-    }
+    const std::vector<double> phi = gaussian_vectors(o.seed + (uint64_t)k + 1, o.npert, ctx[k]->npw_h);
     rc = wdf_model_add_solves(m, ctx[k], o.npert, phi.data(), WDF_MEM_HOST, nullptr);
     if (rc == WDF_ENOCONV) rc = WDF_OK;  // samples of unconverged solves are still usable
   }
@@ -992,6 +1101,113 @@ int wdf_train_preconditioner(wdf_ctx *const *ctx, int n, const wdf_train_opts *o
   }
   *out = m;
   return WDF_OK;
+}
+
+
+int wdf_half_sphere(const double cell[9], double ecut, int32_t *miller, int *npw_h) {
+  if (!cell || !npw_h || !(ecut > 0)) {
+    set_error(WDF_EINVAL, "cell, npw_h and a positive ecut are required");
+    return WDF_EINVAL;
+  }
+  try {
+    const double *A = cell;
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+    if (!(std::fabs(det) > 0)) throw ApiFailure(WDF_EINVAL, "singular cell");
+    // reciprocal rows b_i = 2 pi (A^-1)^T rows; |n_a| <= sqrt(ecut) |a_a| / (2 pi) bounds the box
+    double B[9];
+    const double inv[9] = {(A[4] * A[8] - A[5] * A[7]) / det, (A[2] * A[7] - A[1] * A[8]) / det, (A[1] * A[5] - A[2] * A[4]) / det,
+                           (A[5] * A[6] - A[3] * A[8]) / det, (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
+                           (A[3] * A[7] - A[4] * A[6]) / det, (A[1] * A[6] - A[0] * A[7]) / det, (A[0] * A[4] - A[1] * A[3]) / det};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) B[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
+    int nm[3];
+    for (int a = 0; a < 3; ++a) {
+      const double la = std::sqrt(A[3 * a] * A[3 * a] + A[3 * a + 1] * A[3 * a + 1] + A[3 * a + 2] * A[3 * a + 2]);
+      nm[a] = (int)std::floor(std::sqrt(ecut) * la / (2.0 * M_PI) + 1e-9);
+      if (nm[a] > 4096) throw ApiFailure(WDF_EINVAL, "cutoff too large for the cell");
+    }
+    struct Gv {
+      long long key;
+      int n1, n2, n3;
+    };
+    std::vector<Gv> gv;
+    for (int n3 = 0; n3 <= nm[2]; ++n3)
+      for (int n2 = (n3 > 0 ? -nm[1] : 0); n2 <= nm[1]; ++n2)
+        for (int n1 = ((n3 > 0 || n2 > 0) ? -nm[0] : 0); n1 <= nm[0]; ++n1) {
+          double g[3];
+          for (int c2 = 0; c2 < 3; ++c2) g[c2] = n1 * B[c2] + n2 * B[3 + c2] + n3 * B[6 + c2];
+          const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          if (g2 > ecut * (1.0 + 1e-12)) continue;
+          gv.push_back({std::llround(g2 * 1e9 / ecut), n1, n2, n3});  // shells binned at 1e-9 ecut
+        }
+    std::sort(gv.begin(), gv.end(), [](const Gv &a, const Gv &b) {
+      if (a.key != b.key) return a.key < b.key;
+      if (a.n1 != b.n1) return a.n1 < b.n1;
+      if (a.n2 != b.n2) return a.n2 < b.n2;
+      return a.n3 < b.n3;
+    });
+    if (miller) {
+      if (*npw_h < (int)gv.size()) throw ApiFailure(WDF_EINVAL, "miller has room for fewer triples than the sphere holds");
+      for (size_t i = 0; i < gv.size(); ++i) {
+        miller[3 * i] = gv[i].n1;
+        miller[3 * i + 1] = gv[i].n2;
+        miller[3 * i + 2] = gv[i].n3;
+      }
+    }
+    *npw_h = (int)gv.size();
+    return WDF_OK;
+  } catch (const ApiFailure &f) {
+    set_error(f.code, f.msg);
+    return f.code;
+  } catch (...) {
+    set_error(WDF_ENOMEM, "host allocation failed");
+    return WDF_ENOMEM;
+  }
+}
+
+int wdf_get_gvectors(const wdf_ctx *c, int32_t *miller) {
+  if (!c || !miller) return WDF_EINVAL;
+  std::copy(c->miller.begin(), c->miller.end(), miller);
+  return WDF_OK;
+}
+
+int wdf_reset_error(wdf_ctx *c) {
+  if (!c) return WDF_EINVAL;
+  if (!c->failed) return WDF_OK;
+  if (cudaSetDevice(c->device) != cudaSuccess) return WDF_ESTATE;
+  (void)cudaGetLastError();  // a refused launch leaves a non-sticky error behind
+  const cudaError_t e = c->st ? cudaStreamSynchronize(c->st) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    c->err = std::string("the device reports ") + cudaGetErrorName(e) + ": the context stays unusable";
+    return WDF_ESTATE;
+  }
+  c->failed = false;
+  c->err.clear();
+  return WDF_OK;
+}
+
+int wdf_pdep_davidson_seeded(wdf_ctx *c, int neig, int nbasis_max, int maxiter, double tol, uint64_t seed, double *lambda,
+                             double *phibar, int mem, wdf_stats *st) {
+  if (!c || neig < 1) return WDF_EINVAL;
+  std::vector<double> guess;
+  try {
+    guess = gaussian_vectors(seed, neig, c->npw_h);
+  } catch (...) {
+    set_error(WDF_ENOMEM, "host allocation failed");
+    return WDF_ENOMEM;
+  }
+  if (mem != WDF_MEM_DEVICE) return wdf_pdep_davidson(c, neig, nbasis_max, maxiter, tol, neig, guess.data(), lambda, phibar, mem, st);
+  // device outputs: the start block goes to the device first
+  DBuf dg;
+  int rc = guarded(c, [&] {
+    dg.ensure(sizeof(double) * guess.size());
+    WDF_CUDA_TRY(cudaMemcpy(dg.p, guess.data(), sizeof(double) * guess.size(), cudaMemcpyHostToDevice));
+    return WDF_OK;
+  });
+  if (rc == WDF_OK) rc = wdf_pdep_davidson(c, neig, nbasis_max, maxiter, tol, neig, dg.as<double>(), lambda, phibar, mem, st);
+  (void)cudaSetDevice(c->device);
+  dg.release();
+  return rc;
 }
 
 }  // extern "C"

@@ -145,6 +145,12 @@ inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, di
   }
 }
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device. The
+// attribute belongs to the function, not to a context, so contexts of different grids in one
+// process only ever raise it (a smaller later setting would break the larger context's launches).
+void raise_smem_limit_raw(const void *func, size_t bytes);
+template <typename F> inline void raise_smem_limit(F *func, size_t bytes) { raise_smem_limit_raw((const void *)func, bytes); }
+
 struct CudaFailure {
   cudaError_t err;
   const char *what;

@@ -747,6 +747,28 @@ void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<do
 }
 
 // ---------------------------------------------------------------------------------------------
+// low-rank W_p from PDEP eigenpairs (Eq. 5 without the Xi term)
+
+void wp_apply_internal(wdf_ctx *c, const cplx<double> *phib, const double *coef, int neig, const cplx<double> *x, int nvec,
+                       cplx<double> *y) {
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  c->wp_vx.ensure(sizeof(cplx<double>) * (size_t)nvec * g.ld);
+  c->wp_S.ensure(sizeof(double) * (size_t)neig * nvec);
+  cplx<double> *vx = c->wp_vx.as<cplx<double>>();
+  const double *vh = c->t_vhalf.as<double>();
+  // v^1/2 x; S_a = <phibar_a, v^1/2 x>; y = sum_a phibar_a coef_a S_a; W_p x = v^1/2 y
+  launch("scale_elems", 0, k_scale_elems, dim3(grid_for((size_t)nvec * g.ld)), dim3(256), 0, st, g, vx, x, vh, nvec);
+  WDF_CUDA_TRY(cudaGetLastError());
+  gram<double>(c, phib, neig, vx, nvec, c->wp_S.as<double>(), nvec);
+  WDF_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(cplx<double>) * (size_t)nvec * g.ld, st));
+  launch_lincomb<double>(g, y, nvec, phib, neig, c->wp_S.as<double>(), nvec, coef, 0.0, st);
+  launch("scale_elems", 0, k_scale_elems, dim3(grid_for((size_t)nvec * g.ld)), dim3(256), 0, st, g, y, (const cplx<double> *)y, vh,
+         nvec);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------------
 // block Davidson
 
 static void copy_rows(wdf_ctx *c, cplx<double> *dst, const cplx<double> *src, int n) {
@@ -960,6 +982,63 @@ void ground_state(wdf_ctx *c) {
 }
 
 // tables that depend on the occupied orbitals
+// time the V_loc plane variants (register, Stockham, generic) on a zero column buffer of a few
+// pairs and keep the fastest in f.vloc_variant
+template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const T *vloc) {
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  const int nblk = 32;
+  const size_t bytes = sizeof(cplx<T>) * (size_t)nblk * g.n3 * g.ldcb;
+  DBuf cbuf;
+  cbuf.ensure(bytes);
+  WDF_CUDA_TRY(cudaMemsetAsync(cbuf.p, 0, bytes, st));
+  PlaneArgs<T> pa;
+  pa.cb = cbuf.as<cplx<T>>();
+  pa.field = vloc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = 1e30f;
+  int bestv = 0;
+  if (const char *pin = std::getenv("WDF_PLANE_VARIANT")) {  // fixed choice, e.g. to compare contexts bit for bit
+    const int v = std::atoi(pin);
+    if (v >= 1 && v <= 3 && plane_variant_available<T>(g, v)) {
+      f.vloc_variant = v;
+      cbuf.release();
+      return;
+    }
+  }
+  try {
+    WDF_CUDA_TRY(cudaEventCreate(&e0));
+    WDF_CUDA_TRY(cudaEventCreate(&e1));
+    for (int v = 1; v <= 3; ++v) {
+      if (!plane_variant_available<T>(g, v)) continue;
+      f.vloc_variant = v;
+      launch_plane<T>(f, OP_VLOC, nblk, pa, st);  // warm-up
+      WDF_CUDA_TRY(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) launch_plane<T>(f, OP_VLOC, nblk, pa, st);
+      WDF_CUDA_TRY(cudaEventRecord(e1, st));
+      WDF_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      WDF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bestv = v;
+      }
+    }
+  } catch (...) {
+    if (e0) (void)cudaEventDestroy(e0);
+    if (e1) (void)cudaEventDestroy(e1);
+    cbuf.release();
+    throw;
+  }
+  (void)cudaEventDestroy(e0);
+  (void)cudaEventDestroy(e1);
+  cbuf.release();
+  f.vloc_variant = bestv;
+  if (std::getenv("WDF_TRACE"))
+    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic), %.3f ms per %d pairs\n",
+            bits_of<T>(), bestv, best / 3, nblk);
+}
+
 void finish_setup(wdf_ctx *c) {
   const Geo &g = c->geo;
   cudaStream_t st = c->st;
@@ -1021,6 +1100,11 @@ void finish_setup(wdf_ctx *c) {
     c->psirdf.ensure(sizeof(df64) * (size_t)nocc * c->ngrid);
     launch_convert<double, df64>(g, c->psirdf.as<df64>(), c->psir64.as<double>(), (size_t)nocc * c->ngrid, st);
   }
+  // the V_loc plane kernels of the inner CG and of the residuals: time the variants that exist
+  // for this grid and keep the fastest
+  autotune_vloc<float>(c, c->f32, c->vloc32.as<float>());
+  if (c->opt.precision == WDF_MIXED_DF) autotune_vloc<df64>(c, c->fdf, c->vlocdf.as<df64>());
+  else autotune_vloc<double>(c, c->f64, c->vloc64.as<double>());
   WDF_CUDA_TRY(cudaStreamSynchronize(st));
 }
 

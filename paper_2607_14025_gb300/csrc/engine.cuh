@@ -50,6 +50,7 @@ struct wdf_ctx {
   double cell[9] = {0}, bvec[9] = {0}, omega = 0;
   int npw_h = 0, nproj = 0, nocc = 0;
   std::vector<double> dij, eps;
+  std::vector<int32_t> miller;  // [npw_h][3] as given at setup
   double alpha = 0;
   double gap = 0;  // eps_{nocc+1} - eps_nocc when the library computed the ground state (else 0)
 
@@ -92,6 +93,7 @@ struct wdf_ctx {
   bool has_model = false;
   // training-sample collection (wdf_model_add_solves): sums [3][nocc][ld] over converged solves
   wdf::DBuf mlsums, mlwraw;
+  wdf::DBuf wp_phi, wp_x, wp_y, wp_vx, wp_S, wp_coef;  // wdf_apply_wp
   bool collect = false;
   wdf::DBuf rb, rx, rr, rAx, rwork;        // refinement: b, x, r, A x (FP64), FP32 staging
   wdf::DBuf shift, vidx_dev, thr;          // per-solve shift, orbital index, thresholds
@@ -149,6 +151,11 @@ DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nw
 // x[s] = w[v_s] b[s] elementwise (first iterate of a solve from a per-(v, e) gain table)
 void launch_first_iterate(const Geo &g, cplx<double> *x, const cplx<double> *b, const double *w, const int *vidx, int n,
                           cudaStream_t st);
+
+// W_p x = v^1/2 sum_a phibar_a coef_a <phibar_a, v^1/2 x>, coef_a = lambda_a / (1 - lambda_a)
+// (device array), internal FP64 vectors
+void wp_apply_internal(wdf_ctx *c, const cplx<double> *phib, const double *coef, int neig, const cplx<double> *x, int nvec,
+                       cplx<double> *y);
 
 void ground_state(wdf_ctx *c);     // fills U64 psi rows and c->eps
 void finish_setup(wdf_ctx *c);     // derived tables once psi and eps are known

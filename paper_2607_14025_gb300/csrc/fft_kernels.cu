@@ -271,15 +271,15 @@ template <typename T> size_t plane_smem(const Geo &g) {
 template <typename T>
 void set_fft_smem_limits(const Geo &g) {
   const int zs = (int)zpass_smem<T>(g), ps = (int)plane_smem<T>(g);
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_g2r<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_g2r<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_r2g<T, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_r2g<T, EPI_HSHIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_zpass_r2g<T, EPI_DRHO>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_VLOC>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_G2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_PROD_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane<T, OP_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps));
+  raise_smem_limit(k_zpass_g2r<T, false>, (size_t)(zs));
+  raise_smem_limit(k_zpass_g2r<T, true>, (size_t)(zs));
+  raise_smem_limit(k_zpass_r2g<T, EPI_STORE>, (size_t)(zs));
+  raise_smem_limit(k_zpass_r2g<T, EPI_HSHIFT>, (size_t)(zs));
+  raise_smem_limit(k_zpass_r2g<T, EPI_DRHO>, (size_t)(zs));
+  raise_smem_limit(k_plane<T, OP_VLOC>, (size_t)(ps));
+  raise_smem_limit(k_plane<T, OP_G2R>, (size_t)(ps));
+  raise_smem_limit(k_plane<T, OP_PROD_R2G>, (size_t)(ps));
+  raise_smem_limit(k_plane<T, OP_ACCUM>, (size_t)(ps));
   set_plane_fast_limits<T>(g);
 }
 

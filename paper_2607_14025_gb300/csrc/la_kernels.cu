@@ -975,7 +975,7 @@ void launch_chol_inv(const double *G, int n, double *C, double tol, int *ok, cud
 }
 
 void set_chol_inv_limits(int nmax) {
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_inv_smem(nmax)));
+  raise_smem_limit(k_chol_inv, (size_t)((int)chol_inv_smem(nmax)));
 }
 
 size_t jacobi_work_doubles(int n) {

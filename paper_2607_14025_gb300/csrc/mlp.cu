@@ -408,7 +408,7 @@ int grad_blocks(long long n) {
 size_t mlp_grad_smem() { return sizeof(TrainSmem); }
 
 void set_mlp_limits() {
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)));
+  raise_smem_limit(k_mlp_grad, (size_t)((int)sizeof(TrainSmem)));
 }
 
 int mlp_grad_blocks(long long n) { return grad_blocks(n); }

@@ -451,15 +451,10 @@ __device__ __forceinline__ void line_forward(float2 (&x)[N], const float2 *tw) {
 // natural index held by slot s after line_inverse
 template <int N> __device__ __forceinline__ constexpr int perm_index(int s) { return s / (N / 8) + 8 * (s % (N / 8)); }
 
-// One (pair, z) plane per block of N threads. The column-buffer slice and the V_loc plane arrive
-// with coalesced loads (the slice scattered into a zeroed natural-order tile through jnat), the
-// occupied columns are transformed along n2 by one thread each, every row along n1 with the V_loc
-// product in between by one thread each, the columns back along n2, and the slice leaves with
-// coalesced stores.
 template <int N>
-__global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jnat,
+__global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jidx,
                                                  PlaneArgs<float> pa) {
-  constexpr int P = N + 1;  // tile and V_loc pitch: column accesses hit distinct banks
+  constexpr int P = N + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2 *tw = reinterpret_cast<float2 *>(smraw);
   float2 *tile = tw + N;
@@ -478,19 +473,16 @@ __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict
     vsm[row * P + c + 2] = w.z;
     vsm[row * P + c + 3] = w.w;
   }
-  for (int i = t; i < N * P; i += N) tile[i] = make_float2(0.f, 0.f);
   __syncthreads();
   float2 *cbz = pa.cb + (size_t)q * g.n3 * g.ldcb + (size_t)z * g.ldcb;
-  for (int j = t; j < g.ndisk; j += N) {
-    const int nat = __ldg(jnat + j);
-    tile[(nat / N) * P + nat % N] = cbz[j];
-  }
-  __syncthreads();
   float2 v[N];
   if (t < nx) {  // inverse along n2 of occupied column x
     const int x = xact[t];
 #pragma unroll
-    for (int y = 0; y < N; ++y) v[y] = tile[y * P + x];
+    for (int y = 0; y < N; ++y) {
+      const int jj = __ldg(jidx + y * N + x);
+      v[y] = jj >= 0 ? cbz[jj] : mkc<float>(0.f, 0.f);
+    }
     line_inverse<N>(v, tw);
 #pragma unroll
     for (int s = 0; s < N; ++s) tile[perm_index<N>(s) * P + x] = v[s];
@@ -509,18 +501,16 @@ __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict
       if (x <= xmax || x >= N - xmax) tile[y * P + x] = v[x];
   }
   __syncthreads();
-  if (t < nx) {  // forward along n2 of occupied column x, back into the tile in natural order
+  if (t < nx) {  // forward along n2 of occupied column x, scattered back to the column buffer
     const int x = xact[t];
 #pragma unroll
     for (int s = 0; s < N; ++s) v[s] = tile[perm_index<N>(s) * P + x];
     line_forward<N>(v, tw);
 #pragma unroll
-    for (int y = 0; y < N; ++y) tile[y * P + x] = v[y];
-  }
-  __syncthreads();
-  for (int j = t; j < g.ndisk; j += N) {
-    const int nat = __ldg(jnat + j);
-    cbz[j] = tile[(nat / N) * P + nat % N];
+    for (int y = 0; y < N; ++y) {
+      const int jj = __ldg(jidx + y * N + x);
+      if (jj >= 0) cbz[jj] = v[y];
+    }
   }
 }
 
@@ -537,7 +527,7 @@ template <int N> size_t reg_smem(const Geo &g) {
 }
 
 template <int N> static void launch_reg(const FftCtx<float> &f, int nblk, const PlaneArgs<float> &pa, cudaStream_t st) {
-  launch("plane_vloc", 32, k_plane_reg<N>, dim3(nblk, f.g.n3), dim3(N), reg_smem<N>(f.g), st, f.g, f.tw1, f.jnat, pa);
+  launch("plane_vloc", 32, k_plane_reg<N>, dim3(nblk, f.g.n3), dim3(N), reg_smem<N>(f.g), st, f.g, f.tw1, f.jidx, pa);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -546,7 +536,7 @@ void set_plane_reg_limits(const Geo &g) {
   switch (g.n1) {
 #define X(N)                                                                                                   \
   case N:                                                                                                      \
-    WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane_reg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reg_smem<N>(g))); \
+    raise_smem_limit(k_plane_reg<N>, (size_t)((int)reg_smem<N>(g))); \
     break;
     WDF_REG_SIZES(X)
 #undef X
@@ -571,9 +561,9 @@ template <typename T, int N> size_t fast_smem(const Geo &g) {
 
 template <typename T, int N> static void set_limits(const Geo &g) {
   const int sm = (int)fast_smem<T, N>(g);
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane_fast<T, N, OP_VLOC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane_fast<T, N, OP_G2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_plane_fast<T, N, OP_PROD_R2G>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  raise_smem_limit(k_plane_fast<T, N, OP_VLOC>, (size_t)(sm));
+  raise_smem_limit(k_plane_fast<T, N, OP_G2R>, (size_t)(sm));
+  raise_smem_limit(k_plane_fast<T, N, OP_PROD_R2G>, (size_t)(sm));
 }
 
 template <typename T, int N>
@@ -621,8 +611,10 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
   // the orbital sum of the density response keeps two register blocks across its loop and
   // spills here; it runs once per chi0 application and stays on the generic kernel
   if (op == OP_ACCUM || f.jidx == nullptr) return false;
+  const int v = op == OP_VLOC ? f.vloc_variant : 0;  // chosen at setup by timing (0: this order)
+  if (v == 3) return false;
   if constexpr (std::is_same<T, float>::value) {
-    if (op == OP_VLOC && launch_plane_reg(f, nblk, pa, st)) return true;
+    if (op == OP_VLOC && v != 2 && launch_plane_reg(f, nblk, pa, st)) return true;
   }
   if (!plane_fast_supported(f.g.n1, f.g.n2)) return false;
   switch (f.g.n1) {
@@ -633,6 +625,24 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
     default: return false;
   }
 }
+
+template <typename T> bool plane_variant_available(const Geo &g, int v) {
+  if (v == 3) return true;
+  if (v == 2) return plane_fast_supported(g.n1, g.n2);
+  if (v == 1 && std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == g.n2) {
+    switch (g.n1) {
+#define X(N) \
+  case N: return true;
+      WDF_REG_SIZES(X)
+#undef X
+      default: return false;
+    }
+  }
+  return false;
+}
+template bool plane_variant_available<double>(const Geo &, int);
+template bool plane_variant_available<float>(const Geo &, int);
+template bool plane_variant_available<df64>(const Geo &, int);
 
 template void set_plane_fast_limits<double>(const Geo &);
 template void set_plane_fast_limits<float>(const Geo &);

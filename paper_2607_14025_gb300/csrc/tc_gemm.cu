@@ -375,8 +375,8 @@ bool tc_enabled() {
 int tc_rows(int na) { return ((na + 31) / 32) * 32; }
 
 void set_tc_limits() {
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem(256)));
-  WDF_CUDA_TRY(cudaFuncSetAttribute(k_lincomb_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lincomb_tc_smem()));
+  raise_smem_limit(k_gram_tc, (size_t)((int)gram_tc_smem(256)));
+  raise_smem_limit(k_lincomb_tc, (size_t)((int)lincomb_tc_smem()));
 }
 
 void launch_tc_prep_u(const Geo &g, const float2 *U, int na, float *uwh, float *uwl, float *uth, float *utl, cudaStream_t st) {

@@ -132,6 +132,12 @@ def load(path: str = LIB_PATH):
         "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
         "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
         "wdf_apply_hamiltonian_noalloc": (I, [P, I, P, P]),
+        "wdf_apply_chi0_multi": (I, [I, P, P, P, P, I, P]),
+        "wdf_apply_wp": (I, [P, I, P, P, I, P, P, I]),
+        "wdf_half_sphere": (I, [P, D, P, P]),
+        "wdf_get_gvectors": (I, [P, P]),
+        "wdf_reset_error": (I, [P]),
+        "wdf_pdep_davidson_seeded": (I, [P, I, I, I, D, ctypes.c_uint64, P, P, I, P]),
         "wdf_default_train_opts": (None, [P]),
         "wdf_model_create": (I, [I, ctypes.c_uint64, ctypes.POINTER(P)]),
         "wdf_model_free": (None, [P]),
@@ -380,6 +386,38 @@ class Context:
         self._check(rc, (lam, vec, st))
         return lam, vec, st
 
+    def apply_wp(self, lam, phibar, x):
+        """W_p x from PDEP eigenpairs (wdf_apply_wp; Eq. 5 without Xi)."""
+        keep: list = []
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        pp, mem = _ptr_in(phibar, np.complex128, keep)
+        xp, mem2 = _ptr_in(x, np.complex128, keep)
+        if mem != mem2:
+            raise ValueError("phibar and x must both be host arrays or both device tensors")
+        out, op = self._out_like(x, x.shape[0])
+        self._check(self._lib.wdf_apply_wp(self._ctx, lam.shape[0], lam.ctypes.data, pp, x.shape[0], xp, op, mem))
+        return out
+
+    def gvectors(self) -> np.ndarray:
+        """The context's Miller triples (npw_h, 3)."""
+        m = np.empty((self.npw_h, 3), dtype=np.int32)
+        self._check(self._lib.wdf_get_gvectors(self._ctx, m.ctypes.data))
+        return m
+
+    def reset_error(self):
+        """Clear a recoverable failure (see wdf_reset_error)."""
+        self._check(self._lib.wdf_reset_error(self._ctx))
+
+    def pdep_seeded(self, neig: int, seed: int = 0, nbasis_max: int = 0, maxiter: int = 100, tol: float = 1e-10):
+        """PDEP from a start block the library draws from splitmix64(seed)."""
+        lam = np.empty(neig)
+        vec = np.empty((neig, self.npw_h), dtype=np.complex128)
+        st = Stats()
+        rc = self._lib.wdf_pdep_davidson_seeded(self._ctx, neig, nbasis_max, maxiter, tol, seed, lam.ctypes.data, vec.ctypes.data,
+                                                WDF_MEM_HOST, ctypes.byref(st))
+        self._check(rc, (lam, vec, st))
+        return lam, vec, st
+
     def set_model(self, model: Optional["Model"]):
         """Use a trained model as preconditioner (WDF_PRECOND_LEARNED); None: back to TPA."""
         self._check(self._lib.wdf_set_model(self._ctx, model._m if model is not None else None))
@@ -489,3 +527,35 @@ def train_preconditioner(contexts, npert: int = 8, steps: int = 600, lr: float =
     st = TrainStats()
     _check_global(lib, lib.wdf_train_preconditioner(arr, len(contexts), ctypes.byref(o), ctypes.byref(h), ctypes.byref(st)))
     return Model(_handle=h), st
+
+
+def apply_chi0_multi(contexts, phis):
+    """chi0bar for several systems at once (wdf_apply_chi0_multi): returns (outs, stats).
+
+    ``phis[k]`` are host arrays (npert_k, npw_h of context k); the systems run concurrently.
+    """
+    lib = load()
+    n = len(contexts)
+    keep = [np.ascontiguousarray(p, dtype=np.complex128) for p in phis]
+    outs = [np.empty_like(p) for p in keep]
+    ctxa = (ctypes.c_void_p * n)(*[c._ctx.value for c in contexts])
+    npa = (ctypes.c_int * n)(*[p.shape[0] for p in keep])
+    pa = (ctypes.c_void_p * n)(*[p.ctypes.data for p in keep])
+    oa = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+    st = (Stats * n)()
+    rc = lib.wdf_apply_chi0_multi(n, ctxa, npa, pa, oa, WDF_MEM_HOST, st)
+    if rc == WDF_ENOCONV:
+        raise NotConverged(rc, lib.wdf_last_error(None).decode(), (outs, list(st)))
+    _check_global(lib, rc)
+    return outs, list(st)
+
+
+def half_sphere(cell, ecut: float) -> np.ndarray:
+    """wdf_half_sphere: the canonical Gamma half sphere (npw_h, 3) for a cell and cutoff."""
+    lib = load()
+    c = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    n = ctypes.c_int(0)
+    _check_global(lib, lib.wdf_half_sphere(c.ctypes.data, ecut, None, ctypes.byref(n)))
+    m = np.empty((n.value, 3), dtype=np.int32)
+    _check_global(lib, lib.wdf_half_sphere(c.ctypes.data, ecut, m.ctypes.data, ctypes.byref(n)))
+    return m

@@ -46,6 +46,8 @@ __all__ = [
     "SystemSpec",
     "System",
     "SPECS",
+    "BATCH_GRIDS",
+    "batch_family",
     "spec",
     "make_system",
     "make_perturbations",
@@ -130,6 +132,25 @@ SPECS = {
     "medium": SystemSpec("medium", 20.0, (64, 64, 64), 25.0, 32, 64, 12.0, 1.0, 0.8, -2.0, 5.0, 5.0, 0),
     "precision": SystemSpec("precision", 28.0, (96, 96, 96), 25.0, 128, 256, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, 0),
 }
+
+
+# The batching workload: systems of uneven size on 2,3,5-smooth grids from 32^3 to 80^3, the cell
+# growing with the grid at the spacing of the precision system (L = 28 n / 96 bohr, same cutoff)
+# and one atom per 171 bohr^3 as there, two occupied orbitals per atom, the precision system's
+# wells and projectors. Sizes: 5 atoms / 10 orbitals (32^3) to 74 atoms / 148 orbitals (80^3).
+BATCH_GRIDS = (32, 36, 40, 45, 48, 50, 54, 60, 64, 72, 75, 80, 40, 48, 60, 64)
+
+
+def batch_family(count: int = 16, seed: int = 0) -> list:
+    """Specs of ``count`` systems of the batching workload (deterministic in ``seed``)."""
+    out = []
+    for k in range(count):
+        n = BATCH_GRIDS[k % len(BATCH_GRIDS)]
+        L = n * 28.0 / 96.0
+        natom = max(4, int(round(L ** 3 / 171.0)))
+        out.append(SystemSpec(f"batch{k}", L, (n, n, n), 25.0, natom, 2 * natom, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5,
+                              1000 * seed + k))
+    return out
 
 
 def spec(name: str) -> SystemSpec:

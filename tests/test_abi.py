@@ -106,3 +106,34 @@ def test_without_gpu_setup_reports_state_error():
     with pytest.raises(wdf.WdfError) as e:
         wdf.Context(s)
     assert e.value.code == wdf.WDF_ESTATE
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "ragged", "medium", "precision"])
+def test_half_sphere_matches_the_input_generator(lib, name):
+    # host-only entry point: the library's canonical half sphere equals the one the inputs use
+    from paper_2607_14025_gb300 import wdf
+
+    sp = synth.spec(name)
+    cell = np.eye(3) * sp.L
+    got = wdf.half_sphere(cell, sp.ecut)
+    want = synth.half_sphere(sp.L, sp.ecut)
+    assert np.array_equal(got, want)
+
+
+def test_half_sphere_of_a_skewed_cell_by_brute_force(lib):
+    from paper_2607_14025_gb300 import wdf
+
+    cell = np.array([[9.0, 0.0, 0.0], [2.0, 8.5, 0.0], [1.0, -1.5, 10.0]])
+    ecut = 12.0
+    got = wdf.half_sphere(cell, ecut)
+    B = 2 * np.pi * np.linalg.inv(cell).T
+    r = np.arange(-12, 13)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    g2 = np.sum((n @ B) ** 2, axis=1)
+    half = (n[:, 2] > 0) | ((n[:, 2] == 0) & (n[:, 1] > 0)) | ((n[:, 2] == 0) & (n[:, 1] == 0) & (n[:, 0] >= 0))
+    want = n[(g2 <= ecut) & half]
+    assert len(got) == len(want)
+    assert {tuple(x) for x in got} == {tuple(x) for x in want}
+    gg = np.sum((got @ B) ** 2, axis=1)
+    assert np.all(np.diff(gg) >= -1e-9 * ecut)  # ordered by |G|^2
+    assert tuple(got[0]) == (0, 0, 0)
