@@ -322,7 +322,7 @@ int wdf_train_preconditioner(wdf_ctx *const *ctx, int n, const wdf_train_opts *o
  * lincomb, dot_partial, cg_start, cg_update, cg_direction, cg_scalars, axpby, scale_rows,
  * convert, ext_to_int, int_to_ext, ritz_residual, tpa_table, kinetic, mul_table, check_finite,
  * jac_init, jac_rows, jac_cols, jac_check, jac_sort, split_pairs, scale_elems, gather_shift,
- * sum_chunks, chol_inv, mlp_grad, mlp_reduce, mlp_adam, mlp_table, mlp_accum, mlp_samples. NULL stops timing. Calling it resets the counters. Errors: WDF_EINVAL. */
+ * sum_chunks, chol_inv, compact, tc_prep, mlp_predict, mlp_grad, mlp_reduce, mlp_adam, mlp_table, mlp_accum, mlp_samples. NULL stops timing. Calling it resets the counters. Errors: WDF_EINVAL. */
 int wdf_profile_kernel(wdf_ctx *ctx, const char *kernel);
 
 /* Launches of the selected class since wdf_profile_kernel and their summed device time in

@@ -60,6 +60,12 @@ void launch_zpass_g2r_dir(const FftCtx<T> &f, const PDir<T> &d, int nvec, cplx<T
 template <typename T>
 void launch_zpass_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st);
 template <typename T> void launch_plane(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
+// compile-time n3 transforms (zpass_fast_*.cu); false when the size has none
+template <typename T> bool zpass_fast_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st);
+template <typename T> bool zpass_fast_g2r_dir(const FftCtx<T> &f, const PDir<T> &d, int nvec, cplx<T> *cb, cudaStream_t st);
+template <typename T>
+bool zpass_fast_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st);
+template <typename T> void set_zpass_fast_limits(const Geo &g);
 
 // ---------------------------------------------------------------------------------------------
 // dense linear algebra on blocks of internal vectors (rows of length ld, nint live elements)

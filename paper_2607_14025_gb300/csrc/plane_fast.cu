@@ -17,71 +17,14 @@
 
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "stockham.cuh"
 
 namespace wdf {
-
-// radices: 8 first, then 4, 5, 3, 2
-__host__ __device__ constexpr int rad_at(int n, int p) {
-  int m = n;
-  int idx = 0;
-  const int pr[5] = {8, 4, 5, 3, 2};
-  for (int i = 0; i < 5; ++i) {
-    while (m % pr[i] == 0) {
-      if (idx == p) return pr[i];
-      m /= pr[i];
-      ++idx;
-    }
-  }
-  return 1;
-}
-__host__ __device__ constexpr int nrad(int n) {
-  int c = 0;
-  while (rad_at(n, c) > 1) ++c;
-  return c;
-}
-__host__ __device__ constexpr int ls_at(int n, int p) {  // product of the radices before pass p
-  int l = 1;
-  for (int i = 0; i < p; ++i) l *= rad_at(n, i);
-  return l;
-}
-// forward passes run the radices in reverse order
-__host__ __device__ constexpr int frad_at(int n, int p) { return rad_at(n, nrad(n) - 1 - p); }
-__host__ __device__ constexpr int fls_at(int n, int p) {
-  int l = 1;
-  for (int i = 0; i < p; ++i) l *= frad_at(n, i);
-  return l;
-}
-__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 template <int N> struct PlaneShape {
   static constexpr int threads = (N * N / 16 < 64) ? 64 : ((N * N / 16 + 31) / 32 * 32 > 1024 ? 1024 : (N * N / 16 + 31) / 32 * 32);
   static constexpr int pitch = N + 1;
 };
-
-template <typename T, int R>
-__device__ __forceinline__ void dft_reg(cplx<T> *v, T sg) {
-  if (R == 8) {
-    // radix-2 split into two 4-point DFTs, combined with w8^k = exp(sg 2 pi i k / 8)
-    cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
-    cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
-    small_dft<T>(e, 4, sg);
-    small_dft<T>(o, 4, sg);
-    const T h = (T)0.70710678118654752440;
-    const cplx<T> o1 = mkc<T>(h * (o[1].x - sg * o[1].y), h * (o[1].y + sg * o[1].x));   // o1 (1 + sg i)/sqrt2
-    const cplx<T> o2 = cimul<T>(o[2], sg);                                                  // o2 sg i
-    const cplx<T> o3 = mkc<T>(h * (-o[3].x - sg * o[3].y), h * (-o[3].y + sg * o[3].x));  // o3 (-1 + sg i)/sqrt2
-    v[0] = cadd<T>(e[0], o[0]);
-    v[4] = csub<T>(e[0], o[0]);
-    v[1] = cadd<T>(e[1], o1);
-    v[5] = csub<T>(e[1], o1);
-    v[2] = cadd<T>(e[2], o2);
-    v[6] = csub<T>(e[2], o2);
-    v[3] = cadd<T>(e[3], o3);
-    v[7] = csub<T>(e[3], o3);
-  } else {
-    small_dft<T>(v, R, sg);
-  }
-}
 
 // Pieces of one pass over nlines lines of length N (line l starts at base(l) = lbase[l] or
 // l * lpitch, element t at base + t * es): pass_load reads the R inputs of each task, pass_compute

@@ -1,0 +1,121 @@
+// Compile-time Stockham FFT passes shared by the plane kernels and the n3 transforms.
+//
+// A length-N transform runs its radices 8, 4, 5, 3, 2 (largest first; the forward transform in
+// the reverse order). Pass (radix R, stride Ls): butterfly j reads elements j + r N / R of its
+// line, multiplies element r by w^(r k / (Ls R)) with k = j mod Ls (w = exp(+2 pi i / N) for the
+// inverse, the conjugate for the forward transform), does an R-point DFT in registers and writes
+// element (j / Ls) Ls R + k + r Ls. Input and output are in natural order (no digit reversal).
+#pragma once
+
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace wdf {
+
+// radices: 8 first, then 4, 5, 3, 2
+__host__ __device__ constexpr int rad_at(int n, int p) {
+  int m = n;
+  int idx = 0;
+  const int pr[5] = {8, 4, 5, 3, 2};
+  for (int i = 0; i < 5; ++i) {
+    while (m % pr[i] == 0) {
+      if (idx == p) return pr[i];
+      m /= pr[i];
+      ++idx;
+    }
+  }
+  return 1;
+}
+__host__ __device__ constexpr int nrad(int n) {
+  int c = 0;
+  while (rad_at(n, c) > 1) ++c;
+  return c;
+}
+__host__ __device__ constexpr int ls_at(int n, int p) {  // product of the radices before pass p
+  int l = 1;
+  for (int i = 0; i < p; ++i) l *= rad_at(n, i);
+  return l;
+}
+// forward passes run the radices in reverse order
+__host__ __device__ constexpr int frad_at(int n, int p) { return rad_at(n, nrad(n) - 1 - p); }
+__host__ __device__ constexpr int fls_at(int n, int p) {
+  int l = 1;
+  for (int i = 0; i < p; ++i) l *= frad_at(n, i);
+  return l;
+}
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_reg(cplx<T> *v, T sg) {
+  if (R == 8) {
+    // radix-2 split into two 4-point DFTs, combined with w8^k = exp(sg 2 pi i k / 8)
+    cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    small_dft<T>(e, 4, sg);
+    small_dft<T>(o, 4, sg);
+    const T h = (T)0.70710678118654752440;
+    const cplx<T> o1 = mkc<T>(h * (o[1].x - sg * o[1].y), h * (o[1].y + sg * o[1].x));   // o1 (1 + sg i)/sqrt2
+    const cplx<T> o2 = cimul<T>(o[2], sg);                                                  // o2 sg i
+    const cplx<T> o3 = mkc<T>(h * (-o[3].x - sg * o[3].y), h * (-o[3].y + sg * o[3].x));  // o3 (-1 + sg i)/sqrt2
+    v[0] = cadd<T>(e[0], o[0]);
+    v[4] = csub<T>(e[0], o[0]);
+    v[1] = cadd<T>(e[1], o1);
+    v[5] = csub<T>(e[1], o1);
+    v[2] = cadd<T>(e[2], o2);
+    v[6] = csub<T>(e[2], o2);
+    v[3] = cadd<T>(e[3], o3);
+    v[7] = csub<T>(e[3], o3);
+  } else {
+    small_dft<T>(v, R, sg);
+  }
+}
+
+// One pass over NL lines of length N stored at sm[l * PITCH + t], THREADS threads.
+template <typename T, int N, int P, int SIGN, int NL, int PITCH, int THREADS>
+__device__ __forceinline__ void zline_pass(cplx<T> *sm, const cplx<T> *tw) {
+  constexpr int R = SIGN > 0 ? rad_at(N, P) : frad_at(N, P);
+  constexpr int LS = SIGN > 0 ? ls_at(N, P) : fls_at(N, P);
+  constexpr int TASKS = NL * (N / R);
+  constexpr int TPT = cdiv(TASKS, THREADS);
+  cplx<T> v[TPT][R];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int t = threadIdx.x + u * THREADS;
+    if (TASKS % THREADS == 0 || t < TASKS) {
+      const int l = t % NL, j = t / NL;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u][r] = sm[l * PITCH + j + r * (N / R)];
+      if constexpr (LS > 1) {
+        const int k = j % LS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const cplx<T> w = tw[(r * k * (N / (LS * R))) % N];
+          v[u][r] = (SIGN > 0) ? cmul<T>(v[u][r], w) : cmulc<T>(v[u][r], w);
+        }
+      }
+      dft_reg<T, R>(v[u], (T)SIGN);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int t = threadIdx.x + u * THREADS;
+    if (TASKS % THREADS == 0 || t < TASKS) {
+      const int l = t % NL, j = t / NL;
+      const int k = j % LS, o = (j / LS) * LS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[l * PITCH + o + r * LS] = v[u][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int N, int SIGN, int NL, int PITCH, int THREADS, int P = 0>
+__device__ __forceinline__ void zlines_fft(cplx<T> *sm, const cplx<T> *tw) {
+  if constexpr (P < nrad(N)) {
+    zline_pass<T, N, P, SIGN, NL, PITCH, THREADS>(sm, tw);
+    zlines_fft<T, N, SIGN, NL, PITCH, THREADS, P + 1>(sm, tw);
+  }
+}
+
+}  // namespace wdf

@@ -1,0 +1,4 @@
+// Compile-time n3 transforms, double instances (see zpass_fast_impl.cuh).
+#include "zpass_fast_impl.cuh"
+
+WDF_ZFAST_INST(double)
