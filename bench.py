@@ -52,6 +52,12 @@ ALU_PEAK_SOURCE = {"mixed_df": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (d
                    "fp64": "FP64: measured FMA loop on GB300, 1.19 TFLOP/s"}
 
 
+# DRAM bytes per (pair, z plane) block of k_plane_reg<64> from one ncu capture on the medium
+# system (dram__bytes_read.sum + dram__bytes_write.sum = 210.9 + 167.4 MB over 32,768 blocks;
+# profiles/plane_vloc_f32_medium.md); traffic grows in proportion to the blocks launched
+PLANE_REG64_DRAM_BYTES_PER_BLOCK = (210.873088e6 + 167.385088e6) / 32768
+
+
 def plane_flops(system, npair: int) -> float:
     """FFT flops (5 n log2 n per complex line) of one V_loc plane launch over npair pairs.
 
@@ -335,6 +341,14 @@ def run_gpu(args):
     per_launch_flops = total_flops / max(1, k_launches)
     achieved = total_flops / (k_ms * 1e-3) / 1e12 if k_launches else None
     alu_peak = ALU_PEAK_TFLOPS[args.precision]
+    # DRAM traffic per launch from the ncu capture (FP32 64^3 kernel only), and the algorithmic
+    # bytes: the column-buffer slice read and written (8 B per disk column and z) + V_loc plane
+    blocks_per_launch = k_blocks / max(1, k_launches)
+    full = np.concatenate([s.miller, -s.miller[1:]])
+    ndisk = len({(int(a), int(b)) for a, b, _ in full})
+    alg_bytes = blocks_per_launch * 2 * ndisk * 8
+    traffic = (PLANE_REG64_DRAM_BYTES_PER_BLOCK * blocks_per_launch
+               if args.precision != "fp64" and tuple(s.grid) == (64, 64, 64) else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -353,7 +367,9 @@ def run_gpu(args):
                 "d2h_bytes_per_step": NEIG * s.npw_h * 16 + NEIG * 8},
         "gpu_launches": int(round(launches)),
         "roofline": {"kernel": target, "bound": bound, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                     "algorithmic_bytes_per_launch": alg_bytes,
                      "launches_per_step": k_launches / args.steps, "ms_per_launch": avg_ms,
                      "share_of_step": k_ms / args.steps / ms_dev, "algorithmic_flops_per_launch": per_launch_flops,
                      "flops_per_pair_plane": per_plane_flops, "pair_planes_per_step": k_blocks / args.steps,

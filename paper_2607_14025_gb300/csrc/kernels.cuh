@@ -17,7 +17,8 @@ template <typename T> struct FftCtx {
   const cplx<T> *tw1, *tw2, *tw3;  // exp(2 pi i t / n) per axis
   const int *jidx;                 // [n2][n1] disk column at natural (y, x), or -1
   const int *jnat;                 // [ndisk] natural y * n1 + x of each disk column
-  int vloc_variant = 0;            // V_loc plane kernel: 0 default order, 1 register, 2 Stockham, 3 generic
+  int vloc_variant = 0;            // V_loc plane kernel: 0 default order, 1 register, 2 Stockham, 3 generic,
+                                   // 4 register with two threads per line (n1 = n2 = 64)
 };
 
 template <typename T> struct EpiArgs {
@@ -42,7 +43,7 @@ template <typename T> void set_fft_smem_limits(const Geo &g);
 bool plane_fast_supported(int n1, int n2);
 template <typename T> void set_plane_fast_limits(const Geo &g);
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
-// whether V_loc plane variant v (1 register, 2 Stockham, 3 generic) exists for this geometry
+// whether V_loc plane variant v (1 register, 2 Stockham, 3 generic, 4 two-thread register) exists
 template <typename T> bool plane_variant_available(const Geo &g, int v);
 template <typename T> size_t plane_smem(const Geo &g);
 template <typename T> size_t zpass_smem(const Geo &g);

@@ -457,6 +457,168 @@ __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict
   }
 }
 
+// Two threads per line, N = 64 = 8 x 8: lanes 2i and 2i+1 share a line, each holding 32 values
+// in v[g][e] (g < 4, e < 8). Inverse: lane h first holds x[4h + g + 8 n1] at v[g][n1], transforms
+// the 4 radix-8 groups n2 = 4h + g over n1 with twiddles w^(n2 k1), exchanges the 16 values whose
+// k1 belongs to the other lane (one shuffle each way per value), and transforms over n2; the
+// result X[4h + j + 8 k2] sits at v[k2 % 4][4 (k2 / 4) + j]. The forward transform starts from
+// that distribution (no exchange before its first stage) and ends with Y[4h + g + 8 q1] at
+// v[g][q1], the inverse's input distribution. Half the registers of the one-thread line, so
+// twice the warps per SM at the same shared memory.
+__device__ __forceinline__ void pair_exchange(float2 (&v)[4][8], int h, bool fwd) {
+  // inverse: lane h sends (n2 = 4h + g, k1 = 4(1-h) + j) from v[g][4(1-h) + j] and receives the
+  // partner's (n2 = 4(1-h) + g, k1 = 4h + j) into that slot; forward: the same slots with the
+  // roles of k1 and q2 (see the caller), so both directions exchange v[g][4(1-h) + j]
+  (void)fwd;
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float2 &a = v[g][j], &b = v[g][4 + j];
+      const float2 send = h ? a : b;
+      float2 got;
+      got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+      got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+      if (h) a = got;
+      else b = got;
+    }
+}
+
+__device__ __forceinline__ void line2_inverse(float2 (&v)[4][8], int h, const float2 *tw) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    dft_reg<float, 8>(v[g], 1.f);
+    const int n2 = 4 * h + g;
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) v[g][k1] = cmul<float>(v[g][k1], tw[n2 * k1]);
+  }
+  pair_exchange(v, h, false);
+  // k1 = 4h + j: b[n2] = v[n2 % 4][4 (n2 / 4) + j]; outputs back into the same 8 slots
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 b[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) b[n2] = v[n2 & 3][4 * (n2 >> 2) + j];
+    dft_reg<float, 8>(b, 1.f);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[k2 & 3][4 * (k2 >> 2) + j] = b[k2];
+  }
+}
+
+__device__ __forceinline__ void line2_forward(float2 (&v)[4][8], int h, const float2 *tw) {
+  // k1 = 4h + j, values over k2 at v[k2 % 4][4 (k2 / 4) + j]: transform over k2 -> q2, twiddle
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 b[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) b[k2] = v[k2 & 3][4 * (k2 >> 2) + j];
+    dft_reg<float, 8>(b, -1.f);
+    const int k1 = 4 * h + j;
+#pragma unroll
+    for (int q2 = 0; q2 < 8; ++q2) v[q2 & 3][4 * (q2 >> 2) + j] = q2 == 0 ? b[q2] : cmulc<float>(b[q2], tw[k1 * q2]);
+  }
+  // lane h keeps q2 = 4h + g: it sends (k1 = 4h + j, q2 = 4(1-h) + g) from v[g][4(1-h) + j]
+  pair_exchange(v, h, true);
+  // q2 = 4h + g: a[k1] = v[g][k1]; transform over k1 -> q1; Y[4h + g + 8 q1] at v[g][q1]
+#pragma unroll
+  for (int g = 0; g < 4; ++g) dft_reg<float, 8>(v[g], -1.f);
+}
+
+template <int N>
+__global__ void __launch_bounds__(2 * N, 4) k_plane_reg2(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jidx,
+                                                      PlaneArgs<float> pa) {
+  static_assert(N == 64, "two-thread lines are written for 64 = 8 x 8");
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 *tw = reinterpret_cast<float2 *>(smraw);
+  float2 *tile = tw + N;
+  float *vsm = reinterpret_cast<float *>(tile + N * P);
+  int *xact = reinterpret_cast<int *>(vsm + N * P);
+  const int t = threadIdx.x, z = blockIdx.y, q = blockIdx.x;
+  const int line = t >> 1, h = t & 1;
+  const int nx = g.nxact, xmax = g.xmax;
+  if (t < N) tw[t] = twg[t];
+  for (int i = t; i < nx; i += 2 * N) xact[i] = g.xactn[i];
+  const float4 *vz = reinterpret_cast<const float4 *>(pa.field + (size_t)z * N * N);
+  for (int i = t; i < N * N / 4; i += 2 * N) {  // 16-byte loads, padded rows
+    const int row = i / (N / 4), c = 4 * (i % (N / 4));
+    const float4 w = vz[i];
+    vsm[row * P + c] = w.x;
+    vsm[row * P + c + 1] = w.y;
+    vsm[row * P + c + 2] = w.z;
+    vsm[row * P + c + 3] = w.w;
+  }
+  __syncthreads();
+  float2 *cbz = pa.cb + (size_t)q * g.n3 * g.ldcb + (size_t)z * g.ldcb;
+  float2 v[4][8];
+  const bool warp_cols = (t & ~31) / 2 < nx;  // some line of this warp is an occupied column
+  if (warp_cols) {  // inverse along n2 of occupied column x (lanes of unoccupied lines run on zeros)
+    const bool mine = line < nx;
+    const int x = mine ? xact[line] : 0;
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) {
+        const int y = 4 * h + gg + 8 * n1;
+        const int jj = mine ? __ldg(jidx + y * N + x) : -1;
+        v[gg][n1] = jj >= 0 ? cbz[jj] : make_float2(0.f, 0.f);
+      }
+    line2_inverse(v, h, tw);
+    if (mine)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) tile[(4 * h + j + 8 * k2) * P + x] = v[k2 & 3][4 * (k2 >> 2) + j];
+  }
+  __syncthreads();
+  {  // row y: inverse along n1, V_loc, forward along n1
+    const int y = line;
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) {
+        const int x = 4 * h + gg + 8 * n1;
+        v[gg][n1] = (x <= xmax || x >= N - xmax) ? tile[y * P + x] : make_float2(0.f, 0.f);
+      }
+    line2_inverse(v, h, tw);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        float2 &e = v[k2 & 3][4 * (k2 >> 2) + j];
+        e = cscal<float>(e, vsm[y * P + 4 * h + j + 8 * k2]);
+      }
+    line2_forward(v, h, tw);
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+      for (int q1 = 0; q1 < 8; ++q1) {
+        const int x = 4 * h + gg + 8 * q1;
+        if (x <= xmax || x >= N - xmax) tile[y * P + x] = v[gg][q1];
+      }
+  }
+  __syncthreads();
+  if (warp_cols) {  // forward along n2 of occupied column x, scattered back to the column buffer
+    const bool mine = line < nx;
+    const int x = mine ? xact[line] : 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2)
+        v[k2 & 3][4 * (k2 >> 2) + j] = mine ? tile[(4 * h + j + 8 * k2) * P + x] : make_float2(0.f, 0.f);
+    line2_forward(v, h, tw);
+    if (mine)
+#pragma unroll
+      for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+        for (int q1 = 0; q1 < 8; ++q1) {
+          const int y = 4 * h + gg + 8 * q1;
+          const int jj = __ldg(jidx + y * N + x);
+          if (jj >= 0) cbz[jj] = v[gg][q1];
+        }
+  }
+}
+
 // sizes with the register kernels: N = 8 R2, R2 in {3, 4, 5, 8}
 #define WDF_REG_SIZES(X) X(24) X(32) X(40) X(64)
 
@@ -476,6 +638,7 @@ template <int N> static void launch_reg(const FftCtx<float> &f, int nblk, const 
 
 
 void set_plane_reg_limits(const Geo &g) {
+  if (g.n1 == 64) raise_smem_limit(k_plane_reg2<64>, reg_smem<64>(g));
   switch (g.n1) {
 #define X(N)                                                                                                   \
   case N:                                                                                                      \
@@ -485,6 +648,13 @@ void set_plane_reg_limits(const Geo &g) {
 #undef X
     default: break;
   }
+}
+
+static bool launch_plane_reg2(const FftCtx<float> &f, int nblk, const PlaneArgs<float> &pa, cudaStream_t st) {
+  if (f.g.n1 != 64 || f.g.n2 != 64) return false;
+  launch("plane_vloc", 32, k_plane_reg2<64>, dim3(nblk, f.g.n3), dim3(128), reg_smem<64>(f.g), st, f.g, f.tw1, f.jidx, pa);
+  WDF_CUDA_TRY(cudaGetLastError());
+  return true;
 }
 
 static bool launch_plane_reg(const FftCtx<float> &f, int nblk, const PlaneArgs<float> &pa, cudaStream_t st) {
@@ -557,6 +727,7 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
   const int v = op == OP_VLOC ? f.vloc_variant : 0;  // chosen at setup by timing (0: this order)
   if (v == 3) return false;
   if constexpr (std::is_same<T, float>::value) {
+    if (op == OP_VLOC && v == 4 && launch_plane_reg2(f, nblk, pa, st)) return true;
     if (op == OP_VLOC && v != 2 && launch_plane_reg(f, nblk, pa, st)) return true;
   }
   if (!plane_fast_supported(f.g.n1, f.g.n2)) return false;
@@ -571,6 +742,7 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
 
 template <typename T> bool plane_variant_available(const Geo &g, int v) {
   if (v == 3) return true;
+  if (v == 4) return std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == 64 && g.n2 == 64;
   if (v == 2) return plane_fast_supported(g.n1, g.n2);
   if (v == 1 && std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == g.n2) {
     switch (g.n1) {

@@ -38,8 +38,8 @@ print(json.dumps(st.as_dict()))
 """
 
 
-def run_backend(flag, name, npert, tmp_path, psi=None, eps=None):
-    out = str(tmp_path / f"{name}_{flag}.npy")
+def run_backend(flag, name, npert, tmp_path, psi=None, eps=None, extra_env=None):
+    out = str(tmp_path / f"{name}_{flag}_{sorted((extra_env or {}).items())}.npy".replace(" ", ""))
     pp = ep = ""
     if psi is not None:
         pp, ep = str(tmp_path / "psi.npy"), str(tmp_path / "eps.npy")
@@ -48,6 +48,7 @@ def run_backend(flag, name, npert, tmp_path, psi=None, eps=None):
     env = {k: v for k, v in os.environ.items() if k != "WDF_NO_TC"}
     if flag == "WDF_NO_TC":
         env[flag] = "1"
+    env.update(extra_env or {})
     code = SCRIPT.format(root=ROOT, name=name, npert=npert, psi=pp, eps=ep, out=out)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -83,3 +84,11 @@ def test_medium_system_backends_agree(tmp_path):
     assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
     # the inner iteration counts differ little: both backends carry FP32 accuracy
     assert abs(sa["cg_iters"] - sb["cg_iters"]) <= 0.05 * sb["cg_iters"]
+
+
+def test_plane_kernel_variants_agree_on_the_medium_system(tmp_path):
+    # the one-thread-per-line and the two-threads-per-line register plane kernels (64^3)
+    a, sa = run_backend("tensor_cores", "medium", 5, tmp_path, extra_env={"WDF_PLANE_VARIANT": "1"})
+    b, sb = run_backend("tensor_cores", "medium", 5, tmp_path, extra_env={"WDF_PLANE_VARIANT": "4"})
+    assert sa["converged"] == 1 and sb["converged"] == 1
+    assert np.abs(a - b).max() <= 1e-8 * np.abs(a).max()
