@@ -52,10 +52,14 @@ ALU_PEAK_SOURCE = {"mixed_df": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (d
                    "fp64": "FP64: measured FMA loop on GB300, 1.19 TFLOP/s"}
 
 
-# DRAM bytes per (pair, z plane) block of k_plane_reg<64> from one ncu capture on the medium
-# system (dram__bytes_read.sum + dram__bytes_write.sum = 210.9 + 167.4 MB over 32,768 blocks;
-# profiles/plane_vloc_f32_medium.md); traffic grows in proportion to the blocks launched
-PLANE_REG64_DRAM_BYTES_PER_BLOCK = (210.873088e6 + 167.385088e6) / 32768
+# DRAM bytes per (pair, z plane) unit of the FP32 V_loc plane kernel on the medium system, per
+# kernel variant (the one chosen at setup, wdf_plane_variant), from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum over the units of the captured launch; see
+# profiles/); traffic grows in proportion to the units launched. A variant without a capture of
+# its current code reports null.
+PLANE64_DRAM_BYTES_PER_UNIT = {
+    1: (210.873088e6 + 167.385088e6) / 32768,  # k_plane_reg<64>: 32,768 units
+}
 
 
 def plane_flops(system, npair: int) -> float:
@@ -292,7 +296,8 @@ def run_gpu(args):
         clocks = clk.stop()
         launches = (wdf.launch_count() - nl0) / args.steps
         k_launches, k_ms = ctx.profile_read()
-        k_blocks = ctx.profile_units()  # (pair, z plane) blocks of the timed plane launches
+        k_blocks = ctx.profile_units()  # (pair, z plane) units of the timed plane launches
+        variant = ctx.plane_variant(32 if args.precision != "fp64" else 64)  # plane kernel chosen at setup
         ctx.profile_kernel(None)
         ms_dev = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         # end to end through the C ABI with host buffers
@@ -347,8 +352,8 @@ def run_gpu(args):
     full = np.concatenate([s.miller, -s.miller[1:]])
     ndisk = len({(int(a), int(b)) for a, b, _ in full})
     alg_bytes = blocks_per_launch * 2 * ndisk * 8
-    traffic = (PLANE_REG64_DRAM_BYTES_PER_BLOCK * blocks_per_launch
-               if args.precision != "fp64" and tuple(s.grid) == (64, 64, 64) else None)
+    per_unit = PLANE64_DRAM_BYTES_PER_UNIT.get(variant) if args.precision != "fp64" and tuple(s.grid) == (64, 64, 64) else None
+    traffic = per_unit * blocks_per_launch if per_unit else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -366,7 +371,7 @@ def run_gpu(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,
                 "d2h_bytes_per_step": NEIG * s.npw_h * 16 + NEIG * 8},
         "gpu_launches": int(round(launches)),
-        "roofline": {"kernel": target, "bound": bound, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+        "roofline": {"kernel": target, "variant": variant, "bound": bound, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
                      "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                      "algorithmic_bytes_per_launch": alg_bytes,

@@ -329,10 +329,18 @@ int wdf_profile_kernel(wdf_ctx *ctx, const char *kernel);
  * milliseconds. Synchronises the context's stream. */
 int wdf_profile_read(wdf_ctx *ctx, int64_t *launches, double *ms);
 
-/* Thread blocks launched by the timed launches of the selected class since wdf_profile_kernel:
- * the work units of kernels that give each block one unit (plane_vloc: one block per pair of
- * solves and z plane). Does not synchronise. */
+/* Work units of the timed launches of the selected class since wdf_profile_kernel: thread blocks
+ * for kernels that give each block one unit, and for plane_vloc the (pair of solves, z plane)
+ * units whichever kernel runs it (the persistent variant loops over several units per block).
+ * Does not synchronise. */
 int wdf_profile_units(wdf_ctx *ctx, int64_t *blocks);
+
+/* The V_loc plane kernel chosen at setup by timing for the given arithmetic (bits = 32 FP32,
+ * 64 FP64, 48 double-float): 1 register lines, 2 Stockham, 3 generic, 4 two-thread register
+ * lines, 5 persistent with bulk copies; 0 when that arithmetic has no V_loc plane kernel in this
+ * context (WDF_EINVAL for other bits). Instrumentation: lets a caller match kernel counters taken
+ * on one variant to the kernel that runs. */
+int wdf_plane_variant(const wdf_ctx *ctx, int bits, int *variant);
 
 /* Number of kernel launches the library has made in this process so far (all contexts). */
 int64_t wdf_launch_count(void);

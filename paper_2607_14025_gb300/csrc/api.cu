@@ -232,6 +232,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   g.xact = c->t_xact.as<int>();
   g.xactn = c->t_xactn.as<int>();
   g.xmax = L.xmax;
+  g.ymax = L.ymax;
   g.pos3 = c->t_pos3.as<short>();
   g.g2 = c->t_g2.as<double>();
   c->f64.g = g;
@@ -660,6 +661,16 @@ int wdf_profile_units(wdf_ctx *c, int64_t *blocks) {
   if (!c || !blocks) return WDF_EINVAL;
   *blocks = c->prof.blocks;
   return WDF_OK;
+}
+
+int wdf_plane_variant(const wdf_ctx *c, int bits, int *variant) {
+  if (!c || !variant) return WDF_EINVAL;
+  switch (bits) {
+    case 32: *variant = c->f32.vloc_variant; return WDF_OK;
+    case 64: *variant = c->opt.precision == WDF_MIXED_DF ? 0 : c->f64.vloc_variant; return WDF_OK;
+    case 48: *variant = c->opt.precision == WDF_MIXED_DF ? c->fdf.vloc_variant : 0; return WDF_OK;
+    default: return WDF_EINVAL;
+  }
 }
 
 int64_t wdf_launch_count(void) { return (int64_t)g_launches.load(); }
@@ -1181,6 +1192,7 @@ int wdf_reset_error(wdf_ctx *c) {
     c->err = std::string("the device reports ") + cudaGetErrorName(e) + ": the context stays unusable";
     return WDF_ESTATE;
   }
+  if (c->tcerr.p && cudaMemset(c->tcerr.p, 0, sizeof(int)) != cudaSuccess) return WDF_ESTATE;  // bounded-wait flag
   c->failed = false;
   c->err.clear();
   return WDF_OK;

@@ -85,6 +85,7 @@ struct Geo {
   const int *xact;         // [nxact] tile x positions (pos1) with data
   const int *xactn;        // [nxact] the same columns in natural order (n1 mod N1)
   int xmax;                // largest |n1| of the sphere
+  int ymax;                // largest |n2| of the sphere
   const short *pos3;       // [n3] digit-reversed position along n3
   const double *g2;        // [ld] |G|^2 of each element (0 in padding)
 };
@@ -122,7 +123,7 @@ struct Profiler {
   std::vector<cudaEvent_t> ev;
   size_t used = 0;
   long long count = 0;
-  long long blocks = 0;  // thread blocks of the timed launches (the work units of per-block kernels)
+  long long blocks = 0;  // work units of the timed launches (thread blocks, or (pair, plane) units of persistent kernels)
 };
 extern thread_local Profiler *t_prof;
 extern std::atomic<long long> g_launches;
@@ -131,9 +132,10 @@ void prof_record(cudaStream_t st);  // records the next event of t_prof
 // precision tag of a kernel instance: 64 (FP64), 32 (FP32), 48 (double-float)
 template <typename T> constexpr int bits_of() { return std::is_same<T, df64>::value ? 48 : (int)(8 * sizeof(T)); }
 
+// `units`: the work units the launch processes (thread blocks, except for persistent kernels)
 template <typename... KArgs, typename... Args>
-inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                   Args &&...args) {
+inline void launch_units(const char *cls, int bits, long long units, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, Args &&...args) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   const bool timed = t_prof && t_prof->bits == bits && t_prof->target == cls;
   if (timed) prof_record(st);
@@ -141,8 +143,14 @@ inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, di
   if (timed) {
     prof_record(st);
     ++t_prof->count;
-    t_prof->blocks += (long long)grid.x * grid.y * grid.z;
+    t_prof->blocks += units;
   }
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch(const char *cls, int bits, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   Args &&...args) {
+  launch_units(cls, bits, (long long)grid.x * grid.y * grid.z, k, grid, block, smem, st, std::forward<Args>(args)...);
 }
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device. The

@@ -566,11 +566,11 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
     for (int s = 0; s < n; ++s) iters_total[s] += it[s];
     residual();
   }
-  if (c->tc_on) {
+  {
     int terr = 0;
     WDF_CUDA_TRY(cudaMemcpyAsync(&terr, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     WDF_CUDA_TRY(cudaStreamSynchronize(st));
-    if (terr) throw ApiFailure(WDF_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+    if (terr) throw ApiFailure(WDF_ETIMEOUT, "a kernel gave up waiting for its MMAs or bulk copies");
   }
   ss.converged = conv;
   ss.fallbacks = 0;
@@ -982,12 +982,13 @@ void ground_state(wdf_ctx *c) {
 }
 
 // tables that depend on the occupied orbitals
-// time the V_loc plane variants (register, Stockham, generic) on a zero column buffer of a few
-// pairs and keep the fastest in f.vloc_variant
+// time the V_loc plane variants (register, Stockham, generic, persistent) on a zero column buffer
+// of 128 pairs (enough units for the persistent kernel's pipeline to fill) and keep the fastest in
+// f.vloc_variant
 template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const T *vloc) {
   const Geo &g = c->geo;
   cudaStream_t st = c->st;
-  const int nblk = 32;
+  const int nblk = 128;
   const size_t bytes = sizeof(cplx<T>) * (size_t)nblk * g.n3 * g.ldcb;
   DBuf cbuf;
   cbuf.ensure(bytes);
@@ -1000,7 +1001,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   int bestv = 0;
   if (const char *pin = std::getenv("WDF_PLANE_VARIANT")) {  // fixed choice, e.g. to compare contexts bit for bit
     const int v = std::atoi(pin);
-    if (v >= 1 && v <= 4 && plane_variant_available<T>(g, v)) {
+    if (v >= 1 && v <= 5 && plane_variant_available<T>(f, v)) {
       f.vloc_variant = v;
       cbuf.release();
       return;
@@ -1009,8 +1010,8 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   try {
     WDF_CUDA_TRY(cudaEventCreate(&e0));
     WDF_CUDA_TRY(cudaEventCreate(&e1));
-    for (int v = 1; v <= 4; ++v) {
-      if (!plane_variant_available<T>(g, v)) continue;
+    for (int v = 1; v <= 5; ++v) {
+      if (!plane_variant_available<T>(f, v)) continue;
       f.vloc_variant = v;
       launch_plane<T>(f, OP_VLOC, nblk, pa, st);  // warm-up
       WDF_CUDA_TRY(cudaEventRecord(e0, st));
@@ -1019,6 +1020,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
       WDF_CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
       WDF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (std::getenv("WDF_TRACE")) fprintf(stderr, "[wdf]   plane variant %d (%d-bit): %.3f ms per %d pairs\n", v, bits_of<T>(), ms / 3, nblk);
       if (ms < best) {
         best = ms;
         bestv = v;
@@ -1035,7 +1037,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   cbuf.release();
   f.vloc_variant = bestv;
   if (std::getenv("WDF_TRACE"))
-    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic, 4 two-thread register), %.3f ms per %d pairs\n",
+    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic, 4 two-thread register, 5 persistent), %.3f ms per %d pairs\n",
             bits_of<T>(), bestv, best / 3, nblk);
 }
 
@@ -1083,13 +1085,15 @@ void finish_setup(wdf_ctx *c) {
   c->U32.ensure(sizeof(cplx<float>) * (size_t)M * g.ld);
   launch_convert<double, float>(g, (float *)c->U32.p, (const double *)c->U64.p, 2 * (size_t)M * g.ld, st);
   // tensor-core copies of U for the FP32 projections (at most 256 rows fit one MMA)
+  // one device flag for every kernel with a bounded wait (tensor-core MMAs, bulk copies)
+  c->tcerr.ensure(sizeof(int));
+  WDF_CUDA_TRY(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), st));
+  c->f32.err = c->tcerr.as<int>();
   c->tc_on = tc_enabled() && M >= 1 && M <= 256;
   if (c->tc_on) {
     const int kp = tc_rows(M);
     c->tcU.ensure(sizeof(float) * 2 * (size_t)M * 2 * g.ld);
     c->tcUt.ensure(sizeof(float) * 2 * (size_t)2 * g.ld * kp);
-    c->tcerr.ensure(sizeof(int));
-    WDF_CUDA_TRY(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), st));
     launch_tc_prep_u(g, c->U32.as<float2>(), M, c->tc_uwh(), c->tc_uwl(), c->tc_uth(), c->tc_utl(), st);
   }
   if (c->opt.precision == WDF_MIXED_DF) {  // double-float copies for residuals and density

@@ -25,6 +25,7 @@ struct Layout {
   std::vector<double> g2, vhalf;
   std::vector<int> tile_idx, xact, xactn, jidx, jnat;  // jnat: natural y * n1 + x of each disk column
   int xmax = 0;
+  int ymax = 0;
   std::vector<short> pos3;
   std::vector<int> emap, emap2, econj;  // external half-sphere index -> internal element
   Plan1D P1, P2, P3;

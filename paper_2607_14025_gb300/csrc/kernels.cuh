@@ -18,7 +18,9 @@ template <typename T> struct FftCtx {
   const int *jidx;                 // [n2][n1] disk column at natural (y, x), or -1
   const int *jnat;                 // [ndisk] natural y * n1 + x of each disk column
   int vloc_variant = 0;            // V_loc plane kernel: 0 default order, 1 register, 2 Stockham, 3 generic,
-                                   // 4 register with two threads per line (n1 = n2 = 64)
+                                   // 4 register with two threads per line (n1 = n2 = 64), 5 persistent
+                                   // with bulk copies (64 x 64 planes with a full disk)
+  int *err = nullptr;              // device flag set by a kernel whose bounded wait expired
 };
 
 template <typename T> struct EpiArgs {
@@ -43,8 +45,13 @@ template <typename T> void set_fft_smem_limits(const Geo &g);
 bool plane_fast_supported(int n1, int n2);
 template <typename T> void set_plane_fast_limits(const Geo &g);
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
-// whether V_loc plane variant v (1 register, 2 Stockham, 3 generic, 4 two-thread register) exists
-template <typename T> bool plane_variant_available(const Geo &g, int v);
+// whether V_loc plane variant v (1 register, 2 Stockham, 3 generic, 4 two-thread register,
+// 5 persistent with bulk copies) exists
+template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v);
+// persistent FP32 V_loc plane kernel (plane_pipe.cu); false when the geometry has no instance
+bool plane_pipe_available(const Geo &g, const int *err);
+void set_plane_pipe_limits(const Geo &g);
+bool launch_plane_pipe(const FftCtx<float> &f, int npair, const PlaneArgs<float> &pa, cudaStream_t st);
 template <typename T> size_t plane_smem(const Geo &g);
 template <typename T> size_t zpass_smem(const Geo &g);
 // CG direction update folded into the first transform: p = K r + beta p for active solves

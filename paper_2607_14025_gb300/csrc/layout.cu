@@ -193,6 +193,7 @@ Layout build_layout(const int32_t *miller, int npw_h, const int n[3], const doub
     L.jidx[(size_t)wrapi(b, n[1]) * n[0] + wrapi(a, n[0])] = j;
     L.jnat[j] = wrapi(b, n[1]) * n[0] + wrapi(a, n[0]);
     L.xmax = std::max(L.xmax, std::abs(a));
+    L.ymax = std::max(L.ymax, std::abs(b));
   }
   L.xact.assign(xs.begin(), xs.end());
   L.xactn.assign(xsn.begin(), xsn.end());

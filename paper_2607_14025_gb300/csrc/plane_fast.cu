@@ -18,6 +18,7 @@
 #include "fft.cuh"
 #include "kernels.cuh"
 #include "stockham.cuh"
+#include "plane_reg.cuh"
 
 namespace wdf {
 
@@ -346,55 +347,6 @@ __global__ void __launch_bounds__(PlaneShape<N>::threads) k_plane_fast(Geo g, co
 // carries the two transpositions between columns (n2 transforms) and rows (n1 transforms).
 
 template <int N>
-__device__ __forceinline__ void line_inverse(float2 (&x)[N], const float2 *tw) {
-  constexpr int R2 = N / 8;
-#pragma unroll
-  for (int n2 = 0; n2 < R2; ++n2) {
-    float2 a[8];
-#pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) a[n1] = x[n2 + R2 * n1];
-    dft_reg<float, 8>(a, 1.f);
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) x[n2 + R2 * k1] = (n2 * k1 == 0) ? a[k1] : cmul<float>(a[k1], tw[n2 * k1]);
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < 8; ++k1) {
-    float2 b[R2];
-#pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) b[n2] = x[n2 + R2 * k1];
-    dft_reg<float, R2>(b, 1.f);
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) x[k2 + R2 * k1] = b[k2];
-  }
-}
-
-template <int N>
-__device__ __forceinline__ void line_forward(float2 (&x)[N], const float2 *tw) {
-  constexpr int R2 = N / 8;
-#pragma unroll
-  for (int k1 = 0; k1 < 8; ++k1) {
-    float2 b[R2];
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) b[k2] = x[k2 + R2 * k1];
-    dft_reg<float, R2>(b, -1.f);
-#pragma unroll
-    for (int q2 = 0; q2 < R2; ++q2) x[q2 + R2 * k1] = (k1 * q2 == 0) ? b[q2] : cmulc<float>(b[q2], tw[k1 * q2]);
-  }
-#pragma unroll
-  for (int q2 = 0; q2 < R2; ++q2) {
-    float2 a[8];
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) a[k1] = x[q2 + R2 * k1];
-    dft_reg<float, 8>(a, -1.f);
-#pragma unroll
-    for (int q1 = 0; q1 < 8; ++q1) x[q2 + R2 * q1] = a[q1];
-  }
-}
-
-// natural index held by slot s after line_inverse
-template <int N> __device__ __forceinline__ constexpr int perm_index(int s) { return s / (N / 8) + 8 * (s % (N / 8)); }
-
-template <int N>
 __global__ void __launch_bounds__(N) k_plane_reg(Geo g, const float2 *__restrict__ twg, const int *__restrict__ jidx,
                                                  PlaneArgs<float> pa) {
   constexpr int P = N + 1;
@@ -710,7 +662,10 @@ bool plane_fast_supported(int n1, int n2) {
 }
 
 template <typename T> void set_plane_fast_limits(const Geo &g) {
-  if (std::is_same<T, float>::value && g.n1 == g.n2) set_plane_reg_limits(g);
+  if (std::is_same<T, float>::value && g.n1 == g.n2) {
+    set_plane_reg_limits(g);
+    set_plane_pipe_limits(g);
+  }
   switch (g.n1) {
 #define X(N) \
   case N: set_limits<T, N>(g); break;
@@ -727,6 +682,7 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
   const int v = op == OP_VLOC ? f.vloc_variant : 0;  // chosen at setup by timing (0: this order)
   if (v == 3) return false;
   if constexpr (std::is_same<T, float>::value) {
+    if (op == OP_VLOC && v == 5 && launch_plane_pipe(f, nblk, pa, st)) return true;
     if (op == OP_VLOC && v == 4 && launch_plane_reg2(f, nblk, pa, st)) return true;
     if (op == OP_VLOC && v != 2 && launch_plane_reg(f, nblk, pa, st)) return true;
   }
@@ -740,9 +696,12 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
   }
 }
 
-template <typename T> bool plane_variant_available(const Geo &g, int v) {
+template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v) {
+  const Geo &g = f.g;
   if (v == 3) return true;
+  if (f.jidx == nullptr) return false;
   if (v == 4) return std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == 64 && g.n2 == 64;
+  if (v == 5) return std::is_same<T, float>::value && plane_pipe_available(g, f.err);
   if (v == 2) return plane_fast_supported(g.n1, g.n2);
   if (v == 1 && std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == g.n2) {
     switch (g.n1) {
@@ -755,9 +714,9 @@ template <typename T> bool plane_variant_available(const Geo &g, int v) {
   }
   return false;
 }
-template bool plane_variant_available<double>(const Geo &, int);
-template bool plane_variant_available<float>(const Geo &, int);
-template bool plane_variant_available<df64>(const Geo &, int);
+template bool plane_variant_available<double>(const FftCtx<double> &, int);
+template bool plane_variant_available<float>(const FftCtx<float> &, int);
+template bool plane_variant_available<df64>(const FftCtx<df64> &, int);
 
 template void set_plane_fast_limits<double>(const Geo &);
 template void set_plane_fast_limits<float>(const Geo &);

@@ -155,6 +155,7 @@ def load(path: str = LIB_PATH):
         "wdf_profile_kernel": (I, [P, ctypes.c_char_p]),
         "wdf_profile_read": (I, [P, P, P]),
         "wdf_profile_units": (I, [P, P]),
+        "wdf_plane_variant": (I, [P, I, ctypes.POINTER(I)]),
         "wdf_launch_count": (ctypes.c_int64, []),
         "wdf_strerror": (ctypes.c_char_p, [I]),
         "wdf_last_error": (ctypes.c_char_p, [P]),
@@ -368,8 +369,14 @@ class Context:
         self._check(self._lib.wdf_profile_read(self._ctx, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
 
+    def plane_variant(self, bits: int = 32) -> int:
+        """V_loc plane kernel chosen at setup for the given arithmetic (32, 64 or 48 = double-float)."""
+        v = ctypes.c_int()
+        self._check(self._lib.wdf_plane_variant(self._ctx, int(bits), ctypes.byref(v)))
+        return v.value
+
     def profile_units(self) -> int:
-        """Thread blocks of the timed launches (work units of per-block kernels)."""
+        """Work units of the timed launches: thread blocks, or (pair, z plane) units for plane_vloc."""
         b = ctypes.c_int64()
         self._check(self._lib.wdf_profile_units(self._ctx, ctypes.byref(b)))
         return b.value

@@ -81,6 +81,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.wdf_model_loss_grad(None, None, None) == wdf.WDF_EINVAL
     assert lib.wdf_set_model(None, None) == wdf.WDF_EINVAL
     assert lib.wdf_model_create(0, 0, None) == wdf.WDF_EINVAL
+    assert lib.wdf_plane_variant(None, 32, None) == wdf.WDF_EINVAL
     lib.wdf_model_free(None)  # ignored
 
 
