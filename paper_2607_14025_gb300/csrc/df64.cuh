@@ -30,22 +30,28 @@ struct df64 {
   __host__ __device__ explicit operator float() const { return hi + lo; }
 };
 
+// The error-free steps use the round-to-nearest intrinsics, which the compiler never contracts
+// into fused multiply-adds (a contraction would break the exactness the transformations rely on).
 __device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return df64(s, b - (s - a));
+  const float s = __fadd_rn(a, b);
+  return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
 
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  return df_fast_two_sum(s, e);
+  const df64 s = df_two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, e);
 }
 __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
-  const float p = a.hi * b.hi;
+  const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
@@ -54,5 +60,32 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
+
+// Lazy accumulation of double-float products, sum_k a_k b_k: the compensated dot product of
+// Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005) with FP32 as the working precision. s is
+// the FP32 sum of the leading products; c collects, in FP32, every rounding error: TwoSum of s and
+// each product, TwoProd of the leading parts and the two cross terms of the low parts. Each term
+// costs 12 FP32 operations instead of 18 for a double-float multiply and add. Without
+// renormalisation c would grow like sqrt(k) u |s| and its own rounding with it; df_acc_renorm
+// (TwoSum of s and c) every few terms keeps |c| <= ulp(s), so the result stays within a small
+// multiple of the error of double-float accumulation (~2^-47 per term of the running sum).
+struct DfAcc {
+  float s, c;
+};
+__device__ __forceinline__ void df_acc_fma(DfAcc &acc, df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float ep = __fmaf_rn(a.hi, b.hi, -p);
+  ep = __fmaf_rn(a.hi, b.lo, ep);
+  ep = __fmaf_rn(a.lo, b.hi, ep);
+  const df64 t = df_two_sum(acc.s, p);
+  acc.s = t.hi;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(t.lo, ep));
+}
+__device__ __forceinline__ void df_acc_renorm(DfAcc &acc) {
+  const df64 t = df_two_sum(acc.s, acc.c);
+  acc.s = t.hi;
+  acc.c = t.lo;
+}
+__device__ __forceinline__ df64 df_acc_value(DfAcc acc) { return df_two_sum(acc.s, acc.c); }
 
 }  // namespace wdf

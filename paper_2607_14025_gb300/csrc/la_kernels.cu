@@ -24,6 +24,32 @@ template <typename T> __device__ __forceinline__ PartAcc<T> dre_acc(cplx<T> a, c
   return (A)a.x * (A)b.x + (A)a.y * (A)b.y;
 }
 
+// Accumulators of the Gram and linear-combination kernels: a plain sum of products for FP64 (and
+// FP32) elements; for double-float elements the lazy compensated sum DfAcc (12 FP32 operations a
+// term instead of 18), renormalised every few terms.
+template <typename A> struct AccOf {
+  using type = A;
+};
+template <> struct AccOf<df64> {
+  using type = DfAcc;
+};
+template <typename A> __device__ __forceinline__ void acc_zero(A &a) { a = 0; }
+__device__ __forceinline__ void acc_zero(DfAcc &a) { a.s = a.c = 0.f; }
+// a += x.x y.x + x.y y.y (the real part of conj(x) y)
+template <typename A, typename C> __device__ __forceinline__ void acc_dre(A &a, C x, C y) {
+  a += (A)x.x * (A)y.x + (A)x.y * (A)y.y;
+}
+__device__ __forceinline__ void acc_dre(DfAcc &a, cplx<df64> x, cplx<df64> y) {
+  df_acc_fma(a, x.x, y.x);
+  df_acc_fma(a, x.y, y.y);
+}
+template <typename A, typename B> __device__ __forceinline__ void acc_mac(A &a, B x, B y) { a += x * y; }
+__device__ __forceinline__ void acc_mac(DfAcc &a, df64 x, df64 y) { df_acc_fma(a, x, y); }
+template <typename A> __device__ __forceinline__ void acc_renorm(A &) {}
+__device__ __forceinline__ void acc_renorm(DfAcc &a) { df_acc_renorm(a); }
+template <typename A> __device__ __forceinline__ A acc_value(const A &a) { return a; }
+__device__ __forceinline__ df64 acc_value(const DfAcc &a) { return df_acc_value(a); }
+
 // block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024); result valid in
 // thread 0
 static __device__ double block_sum(double v) {
@@ -60,11 +86,11 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const cplx<T> *__restrict__
   const int ebeg = blockIdx.z * echunk;
   const int eend = min(g.nint, ebeg + echunk);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  Acc acc[4][8];
+  typename AccOf<Acc>::type acc[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0;
+    for (int b = 0; b < 8; ++b) acc_zero(acc[a][b]);
   for (int e0 = ebeg; e0 < eend; e0 += GK) {
     // 16 consecutive threads read 16 consecutive elements of one row
 #pragma unroll
@@ -86,17 +112,23 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const cplx<T> *__restrict__
       Bs[col][row] = b;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < GK; ++k) {
-      cplx<T> av[4], bv[8];
+    for (int k0 = 0; k0 < GK; k0 += 4) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[k][ty * 4 + a];
+      for (int k = k0; k < k0 + 4; ++k) {
+        cplx<T> av[4], bv[8];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) bv[b] = Bs[k][tx + 16 * b];  // consecutive lanes: consecutive banks
+        for (int a = 0; a < 4; ++a) av[a] = As[k][ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) bv[b] = Bs[k][tx + 16 * b];  // consecutive lanes: consecutive banks
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc_dre(acc[a][b], av[a], bv[b]);
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] += (Acc)av[a].x * (Acc)bv[b].x + (Acc)av[a].y * (Acc)bv[b].y;
+        for (int b = 0; b < 8; ++b) acc_renorm(acc[a][b]);  // every 8 terms (double-float only)
     }
     __syncthreads();
   }
@@ -106,7 +138,7 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const cplx<T> *__restrict__
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
-      if (i < na && j < nb) o[(size_t)i * ldo + j] = (double)acc[a][b];
+      if (i < na && j < nb) o[(size_t)i * ldo + j] = (double)acc_value(acc[a][b]);
     }
 }
 
@@ -314,11 +346,14 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
   __shared__ cplx<T> us[LJ][LE];
   const int te = threadIdx.x % 32, ts = threadIdx.x / 32;
   const int e0 = blockIdx.x * LE, s0 = blockIdx.y * LS;
-  Acc ax[4][4], ay[4][4];
+  typename AccOf<Acc>::type ax[4][4], ay[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ax[p][q] = ay[p][q] = 0;
+    for (int q = 0; q < 4; ++q) {
+      acc_zero(ax[p][q]);
+      acc_zero(ay[p][q]);
+    }
   for (int j0 = 0; j0 < nu; j0 += LJ) {
     for (int t = threadIdx.x; t < LJ * LS; t += 256) {
       const int jj = t / LS, ss = t % LS;
@@ -345,9 +380,18 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
       for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          ax[p][q] += c[q] * (Acc)u[p].x;
-          ay[p][q] += c[q] * (Acc)u[p].y;
+          acc_mac(ax[p][q], c[q], (Acc)u[p].x);
+          acc_mac(ay[p][q], c[q], (Acc)u[p].y);
         }
+      if ((jj & 7) == 7 || jj == jn - 1) {  // renormalise every 8 terms (double-float only)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc_renorm(ax[p][q]);
+            acc_renorm(ay[p][q]);
+          }
+      }
     }
     __syncthreads();
   }
@@ -363,11 +407,12 @@ __global__ void __launch_bounds__(256) k_lincomb(Geo g, cplx<T> *__restrict__ Y,
       if (e >= g.nint) continue;
       cplx<T> *y = Y + (size_t)s * g.ld + e;
       cplx<T> yv;
+      const Acc sx = acc_value(ax[p][q]), sy = acc_value(ay[p][q]);
       if (c0 == 0.0) {
-        yv = mkc<T>((T)ax[p][q], (T)ay[p][q]);
+        yv = mkc<T>((T)sx, (T)sy);
       } else {
         const cplx<T> o = *y;
-        yv = mkc<T>((T)((Acc)c0 * (Acc)o.x + ax[p][q]), (T)((Acc)c0 * (Acc)o.y + ay[p][q]));
+        yv = mkc<T>((T)((Acc)c0 * (Acc)o.x + sx), (T)((Acc)c0 * (Acc)o.y + sy));
       }
       *y = yv;
       if (part) {  // partial inner products <P_s, Y_s> over this block's elements
