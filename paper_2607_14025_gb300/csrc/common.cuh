@@ -44,6 +44,13 @@ template <typename T> __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T>
 template <typename T> __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
   return mkc<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+// double-float: each part as one two-product sum (df_dot2)
+template <> __device__ __forceinline__ cplx<df64> cmul<df64>(cplx<df64> a, cplx<df64> b) {
+  return mkc<df64>(df_dot2(a.x, b.x, -a.y, b.y), df_dot2(a.x, b.y, a.y, b.x));
+}
+template <> __device__ __forceinline__ cplx<df64> cmulc<df64>(cplx<df64> a, cplx<df64> b) {
+  return mkc<df64>(df_dot2(a.x, b.x, a.y, b.y), df_dot2(a.y, b.x, -a.x, b.y));
+}
 template <typename T> __device__ __forceinline__ cplx<T> cscal(cplx<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
 template <typename T> __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return mkc<T>(a.x, -a.y); }
 // i * s * a

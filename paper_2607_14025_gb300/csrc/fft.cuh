@@ -21,13 +21,19 @@
 
 namespace wdf {
 
-// r-point DFT in registers, X_k = sum_s x_s exp(sign 2 pi i s k / r), r in {2, 3, 4, 5}.
+// a times SG i for SG = +1 or -1: a swap and a sign change, no multiplication (a double-float
+// multiply by +-1 would cost seven FP32 operations and the compiler cannot drop it)
+template <int SG, typename T> __device__ __forceinline__ cplx<T> cimul_unit(cplx<T> a) {
+  return SG > 0 ? mkc<T>(-a.y, a.x) : mkc<T>(a.y, -a.x);
+}
+
+// r-point DFT in registers, X_k = sum_s x_s exp(SG 2 pi i s k / r), r in {2, 3, 4, 5}, SG = +-1.
 // Constants are cos and sin of 2 pi / 5, 4 pi / 5 and sqrt(3)/2.
-template <typename T>
-__device__ __forceinline__ void small_dft(cplx<T> *x, int r, T sg) {
+template <typename T, int SG>
+__device__ __forceinline__ void small_dft(cplx<T> *x, int r) {
   if (r == 4) {
     cplx<T> a = cadd<T>(x[0], x[2]), b = csub<T>(x[0], x[2]);
-    cplx<T> c = cadd<T>(x[1], x[3]), d = cimul<T>(csub<T>(x[1], x[3]), sg);
+    cplx<T> c = cadd<T>(x[1], x[3]), d = cimul_unit<SG, T>(csub<T>(x[1], x[3]));
     x[0] = cadd<T>(a, c);
     x[1] = cadd<T>(b, d);
     x[2] = csub<T>(a, c);
@@ -40,7 +46,7 @@ __device__ __forceinline__ void small_dft(cplx<T> *x, int r, T sg) {
     const T s3 = (T)0.86602540378443864676;
     cplx<T> t = cadd<T>(x[1], x[2]);
     cplx<T> u = mkc<T>(x[0].x - (T)0.5 * t.x, x[0].y - (T)0.5 * t.y);
-    cplx<T> v = cimul<T>(csub<T>(x[1], x[2]), sg * s3);
+    cplx<T> v = cimul<T>(csub<T>(x[1], x[2]), SG > 0 ? s3 : -s3);
     x[0] = cadd<T>(x[0], t);
     x[1] = cadd<T>(u, v);
     x[2] = csub<T>(u, v);
@@ -51,8 +57,8 @@ __device__ __forceinline__ void small_dft(cplx<T> *x, int r, T sg) {
     cplx<T> b1 = csub<T>(x[1], x[4]), b2 = csub<T>(x[2], x[3]);
     cplx<T> p = mkc<T>(x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y);
     cplx<T> q = mkc<T>(x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y);
-    cplx<T> u = cimul<T>(mkc<T>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y), sg);
-    cplx<T> w = cimul<T>(mkc<T>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y), sg);
+    cplx<T> u = cimul_unit<SG, T>(mkc<T>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+    cplx<T> w = cimul_unit<SG, T>(mkc<T>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
     x[0] = cadd<T>(x[0], cadd<T>(a1, a2));
     x[1] = cadd<T>(p, u);
     x[4] = csub<T>(p, u);
@@ -92,7 +98,7 @@ __device__ void fft_lines(cplx<T> *sm, int nlines, const int *line_base, int lin
 #pragma unroll
         for (int s = 1; s < 5; ++s)
           if (s < r) x[s] = cmul<T>(sm[base + (p0 + s * Lj) * es], tw[s * k1 * tstep]);
-        small_dft<T>(x, r, (T)1);
+        small_dft<T, 1>(x, r);
 #pragma unroll
         for (int s = 0; s < 5; ++s)
           if (s < r) sm[base + (p0 + s * Lj) * es] = x[s];
@@ -100,7 +106,7 @@ __device__ void fft_lines(cplx<T> *sm, int nlines, const int *line_base, int lin
 #pragma unroll
         for (int s = 0; s < 5; ++s)
           if (s < r) x[s] = sm[base + (p0 + s * Lj) * es];
-        small_dft<T>(x, r, (T)-1);
+        small_dft<T, -1>(x, r);
         sm[base + p0 * es] = x[0];
 #pragma unroll
         for (int s = 1; s < 5; ++s)

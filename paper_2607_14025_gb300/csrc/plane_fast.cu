@@ -46,7 +46,7 @@ __device__ __forceinline__ void pass_compute(cplx<T> (&v)[TPT][R], int nlines, c
           v[u][r] = (SIGN > 0) ? cmul<T>(v[u][r], w) : cmulc<T>(v[u][r], w);
         }
       }
-      dft_reg<T, R>(v[u], (T)SIGN);
+      dft_reg<T, R, SIGN>(v[u]);
     }
   }
 }
@@ -439,7 +439,7 @@ __device__ __forceinline__ void pair_exchange(float2 (&v)[4][8], int h, bool fwd
 __device__ __forceinline__ void line2_inverse(float2 (&v)[4][8], int h, const float2 *tw) {
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
-    dft_reg<float, 8>(v[g], 1.f);
+    dft_reg<float, 8, 1>(v[g]);
     const int n2 = 4 * h + g;
 #pragma unroll
     for (int k1 = 1; k1 < 8; ++k1) v[g][k1] = cmul<float>(v[g][k1], tw[n2 * k1]);
@@ -451,7 +451,7 @@ __device__ __forceinline__ void line2_inverse(float2 (&v)[4][8], int h, const fl
     float2 b[8];
 #pragma unroll
     for (int n2 = 0; n2 < 8; ++n2) b[n2] = v[n2 & 3][4 * (n2 >> 2) + j];
-    dft_reg<float, 8>(b, 1.f);
+    dft_reg<float, 8, 1>(b);
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) v[k2 & 3][4 * (k2 >> 2) + j] = b[k2];
   }
@@ -464,7 +464,7 @@ __device__ __forceinline__ void line2_forward(float2 (&v)[4][8], int h, const fl
     float2 b[8];
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) b[k2] = v[k2 & 3][4 * (k2 >> 2) + j];
-    dft_reg<float, 8>(b, -1.f);
+    dft_reg<float, 8, -1>(b);
     const int k1 = 4 * h + j;
 #pragma unroll
     for (int q2 = 0; q2 < 8; ++q2) v[q2 & 3][4 * (q2 >> 2) + j] = q2 == 0 ? b[q2] : cmulc<float>(b[q2], tw[k1 * q2]);
@@ -473,7 +473,7 @@ __device__ __forceinline__ void line2_forward(float2 (&v)[4][8], int h, const fl
   pair_exchange(v, h, true);
   // q2 = 4h + g: a[k1] = v[g][k1]; transform over k1 -> q1; Y[4h + g + 8 q1] at v[g][q1]
 #pragma unroll
-  for (int g = 0; g < 4; ++g) dft_reg<float, 8>(v[g], -1.f);
+  for (int g = 0; g < 4; ++g) dft_reg<float, 8, -1>(v[g]);
 }
 
 template <int N>

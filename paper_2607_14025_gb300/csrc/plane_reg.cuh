@@ -18,7 +18,7 @@ __device__ __forceinline__ void line_inverse(float2 (&x)[N], const float2 *tw) {
     float2 a[8];
 #pragma unroll
     for (int n1 = 0; n1 < 8; ++n1) a[n1] = x[n2 + R2 * n1];
-    dft_reg<float, 8>(a, 1.f);
+    dft_reg<float, 8, 1>(a);
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) x[n2 + R2 * k1] = (n2 * k1 == 0) ? a[k1] : cmul<float>(a[k1], tw[n2 * k1]);
   }
@@ -27,7 +27,7 @@ __device__ __forceinline__ void line_inverse(float2 (&x)[N], const float2 *tw) {
     float2 b[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) b[n2] = x[n2 + R2 * k1];
-    dft_reg<float, R2>(b, 1.f);
+    dft_reg<float, R2, 1>(b);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) x[k2 + R2 * k1] = b[k2];
   }
@@ -41,7 +41,7 @@ __device__ __forceinline__ void line_forward(float2 (&x)[N], const float2 *tw) {
     float2 b[R2];
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) b[k2] = x[k2 + R2 * k1];
-    dft_reg<float, R2>(b, -1.f);
+    dft_reg<float, R2, -1>(b);
 #pragma unroll
     for (int q2 = 0; q2 < R2; ++q2) x[q2 + R2 * k1] = (k1 * q2 == 0) ? b[q2] : cmulc<float>(b[q2], tw[k1 * q2]);
   }
@@ -50,7 +50,7 @@ __device__ __forceinline__ void line_forward(float2 (&x)[N], const float2 *tw) {
     float2 a[8];
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) a[k1] = x[q2 + R2 * k1];
-    dft_reg<float, 8>(a, -1.f);
+    dft_reg<float, 8, -1>(a);
 #pragma unroll
     for (int q1 = 0; q1 < 8; ++q1) x[q2 + R2 * q1] = a[q1];
   }

@@ -45,18 +45,19 @@ __host__ __device__ constexpr int fls_at(int n, int p) {
 }
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 
-template <typename T, int R>
-__device__ __forceinline__ void dft_reg(cplx<T> *v, T sg) {
+template <typename T, int R, int SG>
+__device__ __forceinline__ void dft_reg(cplx<T> *v) {
   if (R == 8) {
-    // radix-2 split into two 4-point DFTs, combined with w8^k = exp(sg 2 pi i k / 8)
+    // radix-2 split into two 4-point DFTs, combined with w8^k = exp(SG 2 pi i k / 8)
     cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
     cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
-    small_dft<T>(e, 4, sg);
-    small_dft<T>(o, 4, sg);
+    small_dft<T, SG>(e, 4);
+    small_dft<T, SG>(o, 4);
     const T h = (T)0.70710678118654752440;
-    const cplx<T> o1 = mkc<T>(h * (o[1].x - sg * o[1].y), h * (o[1].y + sg * o[1].x));   // o1 (1 + sg i)/sqrt2
-    const cplx<T> o2 = cimul<T>(o[2], sg);                                                  // o2 sg i
-    const cplx<T> o3 = mkc<T>(h * (-o[3].x - sg * o[3].y), h * (-o[3].y + sg * o[3].x));  // o3 (-1 + sg i)/sqrt2
+    // o1 (1 + SG i)/sqrt2, o2 SG i, o3 (-1 + SG i)/sqrt2
+    const cplx<T> o1 = SG > 0 ? mkc<T>(h * (o[1].x - o[1].y), h * (o[1].y + o[1].x)) : mkc<T>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    const cplx<T> o2 = cimul_unit<SG, T>(o[2]);
+    const cplx<T> o3 = SG > 0 ? mkc<T>(h * (-o[3].x - o[3].y), h * (-o[3].y + o[3].x)) : mkc<T>(h * (o[3].y - o[3].x), h * (-o[3].y - o[3].x));
     v[0] = cadd<T>(e[0], o[0]);
     v[4] = csub<T>(e[0], o[0]);
     v[1] = cadd<T>(e[1], o1);
@@ -66,7 +67,7 @@ __device__ __forceinline__ void dft_reg(cplx<T> *v, T sg) {
     v[3] = cadd<T>(e[3], o3);
     v[7] = csub<T>(e[3], o3);
   } else {
-    small_dft<T>(v, R, sg);
+    small_dft<T, SG>(v, R);
   }
 }
 
@@ -93,7 +94,7 @@ __device__ __forceinline__ void zline_pass(cplx<T> *sm, const cplx<T> *tw) {
           v[u][r] = (SIGN > 0) ? cmul<T>(v[u][r], w) : cmulc<T>(v[u][r], w);
         }
       }
-      dft_reg<T, R>(v[u], (T)SIGN);
+      dft_reg<T, R, SIGN>(v[u]);
     }
   }
   __syncthreads();
