@@ -1001,7 +1001,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   int bestv = 0;
   if (const char *pin = std::getenv("WDF_PLANE_VARIANT")) {  // fixed choice, e.g. to compare contexts bit for bit
     const int v = std::atoi(pin);
-    if (v >= 1 && v <= 5 && plane_variant_available<T>(f, v)) {
+    if (v >= 1 && v <= 6 && plane_variant_available<T>(f, v)) {
       f.vloc_variant = v;
       cbuf.release();
       return;
@@ -1010,7 +1010,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   try {
     WDF_CUDA_TRY(cudaEventCreate(&e0));
     WDF_CUDA_TRY(cudaEventCreate(&e1));
-    for (int v = 1; v <= 5; ++v) {
+    for (int v = 1; v <= 6; ++v) {
       if (!plane_variant_available<T>(f, v)) continue;
       f.vloc_variant = v;
       launch_plane<T>(f, OP_VLOC, nblk, pa, st);  // warm-up
@@ -1037,7 +1037,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   cbuf.release();
   f.vloc_variant = bestv;
   if (std::getenv("WDF_TRACE"))
-    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic, 4 two-thread register, 5 persistent), %.3f ms per %d pairs\n",
+    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic, 4 two-thread register, 5 persistent, 6 double-float), %.3f ms per %d pairs\n",
             bits_of<T>(), bestv, best / 3, nblk);
 }
 

@@ -19,7 +19,8 @@ template <typename T> struct FftCtx {
   const int *jnat;                 // [ndisk] natural y * n1 + x of each disk column
   int vloc_variant = 0;            // V_loc plane kernel: 0 default order, 1 register, 2 Stockham, 3 generic,
                                    // 4 register with two threads per line (n1 = n2 = 64), 5 persistent
-                                   // with bulk copies (64 x 64 planes with a full disk)
+                                   // with bulk copies (64 x 64 planes with a full disk), 6 double-float
+                                   // one task per thread (64 x 64)
   int *err = nullptr;              // device flag set by a kernel whose bounded wait expired
 };
 
@@ -46,12 +47,16 @@ bool plane_fast_supported(int n1, int n2);
 template <typename T> void set_plane_fast_limits(const Geo &g);
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st);
 // whether V_loc plane variant v (1 register, 2 Stockham, 3 generic, 4 two-thread register,
-// 5 persistent with bulk copies) exists
+// 5 persistent with bulk copies, 6 double-float one task per thread) exists
 template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v);
 // persistent FP32 V_loc plane kernel (plane_pipe.cu); false when the geometry has no instance
 bool plane_pipe_available(const Geo &g, const int *err);
 void set_plane_pipe_limits(const Geo &g);
 bool launch_plane_pipe(const FftCtx<float> &f, int npair, const PlaneArgs<float> &pa, cudaStream_t st);
+// double-float 64 x 64 plane kernel (plane_df.cu) for OP_VLOC, OP_PROD_R2G and OP_ACCUM
+bool plane_df_available(const Geo &g, const int *jidx);
+void set_plane_df_limits(const Geo &g);
+bool launch_plane_df(const FftCtx<df64> &f, int op, int nblk, const PlaneArgs<df64> &pa, cudaStream_t st);
 template <typename T> size_t plane_smem(const Geo &g);
 template <typename T> size_t zpass_smem(const Geo &g);
 // CG direction update folded into the first transform: p = K r + beta p for active solves

@@ -666,6 +666,7 @@ template <typename T> void set_plane_fast_limits(const Geo &g) {
     set_plane_reg_limits(g);
     set_plane_pipe_limits(g);
   }
+  if (std::is_same<T, df64>::value) set_plane_df_limits(g);
   switch (g.n1) {
 #define X(N) \
   case N: set_limits<T, N>(g); break;
@@ -678,8 +679,14 @@ template <typename T> void set_plane_fast_limits(const Geo &g) {
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st) {
   // the orbital sum of the density response keeps two register blocks across its loop and
   // spills here; it runs once per chi0 application and stays on the generic kernel
-  if (op == OP_ACCUM || f.jidx == nullptr) return false;
   const int v = op == OP_VLOC ? f.vloc_variant : 0;  // chosen at setup by timing (0: this order)
+  if constexpr (std::is_same<T, df64>::value) {
+    // the double-float 64 x 64 kernel: V_loc when the setup timing chose it, the product and the
+    // orbital sum whenever it exists
+    const bool use = op == OP_VLOC ? v == 6 : (op == OP_PROD_R2G || op == OP_ACCUM);
+    if (use && launch_plane_df(f, op, nblk, pa, st)) return true;
+  }
+  if (op == OP_ACCUM || f.jidx == nullptr) return false;
   if (v == 3) return false;
   if constexpr (std::is_same<T, float>::value) {
     if (op == OP_VLOC && v == 5 && launch_plane_pipe(f, nblk, pa, st)) return true;
@@ -702,6 +709,7 @@ template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v) {
   if (f.jidx == nullptr) return false;
   if (v == 4) return std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == 64 && g.n2 == 64;
   if (v == 5) return std::is_same<T, float>::value && plane_pipe_available(g, f.err);
+  if (v == 6) return std::is_same<T, df64>::value && plane_df_available(g, f.jidx);
   if (v == 2) return plane_fast_supported(g.n1, g.n2);
   if (v == 1 && std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == g.n2) {
     switch (g.n1) {

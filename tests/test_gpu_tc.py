@@ -95,3 +95,13 @@ def test_plane_kernel_variants_agree_on_the_medium_system(variant, tmp_path):
     assert sa["converged"] == 1 and sb["converged"] == 1
     assert np.abs(a - b).max() <= 1e-8 * np.abs(a).max()
     assert abs(sa["cg_iters"] - sb["cg_iters"]) <= 0.02 * sa["cg_iters"]
+
+
+def test_double_float_plane_kernel_agrees_on_the_medium_system(tmp_path):
+    # the 64 x 64 double-float plane kernel (residual V_loc product, right-hand-side product and
+    # density sum, one radix-8 task per thread) against the general Stockham and generic kernels
+    a, sa = run_backend("tensor_cores", "medium", 5, tmp_path)
+    b, sb = run_backend("tensor_cores", "medium", 5, tmp_path, extra_env={"WDF_NO_DF_PLANE": "1"})
+    assert sa["converged"] == 1 and sb["converged"] == 1
+    assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
+    assert abs(sa["cg_iters"] - sb["cg_iters"]) <= 0.02 * sb["cg_iters"]
