@@ -59,6 +59,7 @@ ALU_PEAK_SOURCE = {"mixed_df": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (d
 # its current code reports null.
 PLANE64_DRAM_BYTES_PER_UNIT = {
     1: (210.873088e6 + 167.385088e6) / 32768,  # k_plane_reg<64>: 32,768 units
+    5: (210.877440e6 + 149.595648e6) / 32768,  # k_plane_pipe<15>: 32,768 units
 }
 
 

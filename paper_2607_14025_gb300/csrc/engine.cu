@@ -230,6 +230,26 @@ static std::vector<double> to_host(wdf_ctx *c, const double *d, size_t n) {
 // ---------------------------------------------------------------------------------------------
 // operators
 
+// Pairs of solves per pass of the three FFT kernels (n3 inverse, plane, n3 forward) of an operator
+// application. With a budget of B MB the column buffer of one pass (n3 ldcb complex values per
+// pair) stays within B MB, so the plane kernel and the forward n3 transforms could read what the
+// inverse ones wrote from L2 (129 MB) instead of HBM. Measured on the 64^3 system (8,192 solves):
+// 443 ms per step in one pass, 458 / 465 / 481 ms with 96 / 64 / 32 MB passes; the extra launches
+// and the shorter loops of the persistent plane kernel cost more than the L2 residency saves, so
+// the default is one pass. WDF_FFT_CHUNK_MB sets the budget (0 or unset: one pass).
+static int fft_chunk_pairs(const Geo &g, size_t elem_bytes, int npair) {
+  static const long budget_mb = [] {
+    const char *e = std::getenv("WDF_FFT_CHUNK_MB");
+    return e ? std::atol(e) : 0L;
+  }();
+  if (budget_mb <= 0 || npair <= 1) return std::max(1, npair);
+  const size_t per_pair = elem_bytes * (size_t)g.n3 * g.ldcb;
+  const int cp = (int)std::max<size_t>(1, ((size_t)budget_mb << 20) / per_pair);
+  if (cp >= npair) return npair;
+  const int nchunk = (npair + cp - 1) / cp;
+  return (npair + nchunk - 1) / nchunk;  // even chunks
+}
+
 // Y = (H - shift_s) X (+ alpha P X when with_alpha); H = 1/2|G|^2 + V_loc + sum_j beta_j D_j beta_j^T
 template <typename T>
 void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const double *shift, bool with_alpha) {
@@ -238,19 +258,24 @@ void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const doubl
   const Geo &g = c->geo;
   wdf_ctx::Cg &w = Prec<T>::cg(c);
   const int npair = (n + 1) / 2;
-  w.cb.ensure(sizeof(cplx<T>) * (size_t)npair * g.n3 * g.ldcb);
+  const int cp = fft_chunk_pairs(g, sizeof(cplx<T>), npair);
+  w.cb.ensure(sizeof(cplx<T>) * (size_t)cp * g.n3 * g.ldcb);
   cplx<T> *cb = w.cb.as<cplx<T>>();
-  launch_zpass_g2r<T>(f, X, n, cb, c->st);
-  PlaneArgs<T> pa;
-  pa.cb = cb;
-  pa.field = Prec<T>::vloc(c);
-  launch_plane<T>(f, OP_VLOC, npair, pa, c->st);
-  EpiArgs<T> ea;
-  ea.Y = Y;
-  ea.X = X;
-  ea.shift = shift ? shift : zeros(c, n);
-  ea.scale = (T)(1.0 / (double)c->ngrid);
-  launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, n, ea, c->st);
+  const double *sh = shift ? shift : zeros(c, n);
+  for (int p0 = 0; p0 < npair; p0 += cp) {
+    const int s0 = 2 * p0, ns = std::min(n - s0, 2 * cp), np = (ns + 1) / 2;
+    launch_zpass_g2r<T>(f, X + (size_t)s0 * g.ld, ns, cb, c->st);
+    PlaneArgs<T> pa;
+    pa.cb = cb;
+    pa.field = Prec<T>::vloc(c);
+    launch_plane<T>(f, OP_VLOC, np, pa, c->st);
+    EpiArgs<T> ea;
+    ea.Y = Y + (size_t)s0 * g.ld;
+    ea.X = X + (size_t)s0 * g.ld;
+    ea.shift = sh + s0;
+    ea.scale = (T)(1.0 / (double)c->ngrid);
+    launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, ns, ea, c->st);
+  }
   const int M = c->nproj + (with_alpha ? c->nocc : 0);
   if (M > 0) {
     w.S.ensure(sizeof(double) * (size_t)M * n);
@@ -269,20 +294,34 @@ static int apply_operator_cg(wdf_ctx *c, cplx<T> *X, cplx<T> *Y, int n, const do
   const Geo &g = c->geo;
   wdf_ctx::Cg &w = Prec<T>::cg(c);
   const int npair = (n + 1) / 2;
-  w.cb.ensure(sizeof(cplx<T>) * (size_t)npair * g.n3 * g.ldcb);
+  const int cp = fft_chunk_pairs(g, sizeof(cplx<T>), npair);
+  w.cb.ensure(sizeof(cplx<T>) * (size_t)cp * g.n3 * g.ldcb);
   cplx<T> *cb = w.cb.as<cplx<T>>();
-  if (dir) launch_zpass_g2r_dir<T>(f, *dir, n, cb, c->st);
-  else launch_zpass_g2r<T>(f, X, n, cb, c->st);
-  PlaneArgs<T> pa;
-  pa.cb = cb;
-  pa.field = Prec<T>::vloc(c);
-  launch_plane<T>(f, OP_VLOC, npair, pa, c->st);
-  EpiArgs<T> ea;
-  ea.Y = Y;
-  ea.X = X;
-  ea.shift = shift;
-  ea.scale = (T)(1.0 / (double)c->ngrid);
-  launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, n, ea, c->st);
+  for (int p0 = 0; p0 < npair; p0 += cp) {  // chunks of pairs whose column buffer stays in L2
+    const int s0 = 2 * p0, ns = std::min(n - s0, 2 * cp), np = (ns + 1) / 2;
+    const size_t off = (size_t)s0 * g.ld;
+    if (dir) {
+      PDir<T> d = *dir;
+      d.p += off;
+      d.r += off;
+      d.vidx += s0;
+      d.active += s0;
+      d.beta += s0;
+      launch_zpass_g2r_dir<T>(f, d, ns, cb, c->st);
+    } else {
+      launch_zpass_g2r<T>(f, X + off, ns, cb, c->st);
+    }
+    PlaneArgs<T> pa;
+    pa.cb = cb;
+    pa.field = Prec<T>::vloc(c);
+    launch_plane<T>(f, OP_VLOC, np, pa, c->st);
+    EpiArgs<T> ea;
+    ea.Y = Y + off;
+    ea.X = X + off;
+    ea.shift = shift + s0;
+    ea.scale = (T)(1.0 / (double)c->ngrid);
+    launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, ns, ea, c->st);
+  }
   const int M = c->nproj + c->nocc;
   w.S.ensure(sizeof(double) * (size_t)M * n);
   if constexpr (std::is_same<T, float>::value) {

@@ -105,3 +105,13 @@ def test_double_float_plane_kernel_agrees_on_the_medium_system(tmp_path):
     assert sa["converged"] == 1 and sb["converged"] == 1
     assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
     assert abs(sa["cg_iters"] - sb["cg_iters"]) <= 0.02 * sb["cg_iters"]
+
+
+def test_l2_chunked_fft_passes_are_bitwise_identical(tmp_path):
+    # the three FFT kernels of an operator application in chunks of pairs (a 1 MB column-buffer
+    # budget: two pairs per chunk on the 64^3 grid) against one pass over all pairs
+    a, sa = run_backend("tensor_cores", "medium", 5, tmp_path, extra_env={"WDF_FFT_CHUNK_MB": "0"})
+    b, sb = run_backend("tensor_cores", "medium", 5, tmp_path, extra_env={"WDF_FFT_CHUNK_MB": "1"})
+    assert sa["converged"] == 1 and sb["converged"] == 1
+    assert np.array_equal(a, b)
+    assert sa["cg_iters"] == sb["cg_iters"]
