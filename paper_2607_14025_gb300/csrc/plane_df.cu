@@ -116,7 +116,7 @@ __device__ __forceinline__ void df_phases(const DfGeo &d, int ph0, int ph1, cd (
 }
 
 template <int OP>
-__global__ void __launch_bounds__(kThreads, 1) k_plane_df(Geo g, const cd *__restrict__ twg, const int *__restrict__ jidx,
+__global__ void __launch_bounds__(kThreads, OP == OP_ACCUM ? 1 : 2) k_plane_df(Geo g, const cd *__restrict__ twg, const int *__restrict__ jidx,
                                                          PlaneArgs<df64> pa) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cd *tw = reinterpret_cast<cd *>(smraw);
