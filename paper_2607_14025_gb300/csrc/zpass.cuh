@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(kThreads) k_zpass_r2g(const cplx<T> *__restric
   const int kend = min(k0 + kZCols, g.K);
   const int ncol = kend - k0;
   const cplx<T> *in = cb + (size_t)q * n3 * g.ldcb;
-  for (int it = threadIdx.x; it < n3 * nlines; it += blockDim.x) {
+  // column-buffer element `it` of this block: (z, c2) with c2 < kZCols the rep columns, the rest
+  // their mirrors; zero outside the sphere's columns
+  auto fetch = [&](int it) {
     const int z = it / nlines, c2 = it - z * nlines;
     cplx<T> v = mkc<T>(0, 0);
     if (c2 < kZCols) {
@@ -107,7 +109,31 @@ __global__ void __launch_bounds__(kThreads) k_zpass_r2g(const cplx<T> *__restric
       const int c = c2 - kZCols, k = k0 + c;
       if (c < ncol && k >= 1) v = in[(size_t)z * g.ldcb + g.K - 1 + k];
     }
-    sm[c2 * pitch + z] = v;
+    return v;
+  };
+  if constexpr (N3 > 0) {
+    // all of a thread's loads first (a compile-time count), then the shared-memory stores: the
+    // loads are in flight together instead of one at a time
+    constexpr int TOT = N3 * 2 * kZCols, NIT = (TOT + kThreads - 1) / kThreads;
+    cplx<T> vv[NIT];
+#pragma unroll
+    for (int u = 0; u < NIT; ++u) {
+      const int it = threadIdx.x + u * kThreads;
+      vv[u] = (TOT % kThreads == 0 || it < TOT) ? fetch(it) : mkc<T>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < NIT; ++u) {
+      const int it = threadIdx.x + u * kThreads;
+      if (TOT % kThreads == 0 || it < TOT) {
+        const int z = it / nlines, c2 = it - z * nlines;
+        sm[c2 * pitch + z] = vv[u];
+      }
+    }
+  } else {
+    for (int it = threadIdx.x; it < n3 * nlines; it += blockDim.x) {
+      const int z = it / nlines, c2 = it - z * nlines;
+      sm[c2 * pitch + z] = fetch(it);
+    }
   }
   __syncthreads();
   if constexpr (N3 > 0) zlines_fft<T, N3, -1, 2 * kZCols, N3 + 1, kThreads>(sm, tw);
