@@ -903,6 +903,7 @@ DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nw
   c->dv_theta.ensure(sizeof(double) * nbmax);
   c->dv_jac.ensure(sizeof(double) * jacobi_work_doubles(nbmax));
   c->dv_jint.ensure(sizeof(int) * 4);
+  WDF_CUDA_TRY(cudaMemsetAsync(c->dv_jint.p, 0, sizeof(int) * 4, st));
   c->dv_small.ensure(sizeof(double) * (size_t)std::max(nbmax, n0) * 2);
   c->dv_neg.ensure(sizeof(double) * (size_t)std::max(nbmax, n0));
   {
@@ -931,6 +932,12 @@ DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nw
     dots<double>(c, R, R, k, c->dv_small.as<double>());
     rn = to_host(c, c->dv_small.as<double>(), k);
     th = to_host(c, theta, k);
+    {  // the eigensolve's grid barrier gives up (and flags it) instead of waiting forever
+      int jerr = 0;
+      WDF_CUDA_TRY(cudaMemcpyAsync(&jerr, c->dv_jint.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+      WDF_CUDA_TRY(cudaStreamSynchronize(st));
+      if (jerr) throw ApiFailure(WDF_ETIMEOUT, "the subspace eigensolver gave up waiting at a grid barrier");
+    }
     bool all = true;
     std::vector<int> unconv;
     for (int a = 0; a < k; ++a) {

@@ -1023,6 +1023,109 @@ void set_chol_inv_limits(int nmax) {
   raise_smem_limit(k_chol_inv, (size_t)((int)chol_inv_smem(nmax)));
 }
 
+// The whole eigensolve in one cooperative launch: block b of m/2 owns pair b of every round, a
+// grid barrier separates the row rotations of a round from its column rotations and from the next
+// round, and block 0 tests convergence after each sweep (the same rotations, order and test as
+// the kernels above, without ~2 m launches per sweep). The barrier counts arrivals and bumps a
+// generation number; a block waits for the bump with a bounded number of polls and, on expiry,
+// sets the error flag and returns (the others then expire at their next barrier). Matrix entries
+// written by other blocks are read past L1 (ld.global.cg), which is not coherent across SMs.
+constexpr long kGridBarrierLimit = 1L << 24;
+
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g0 = *(volatile unsigned *)gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long it = 0;
+      while (*(volatile unsigned *)gen == g0) {
+        if (++it > kGridBarrierLimit) {
+          ok = 0;
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// iw: [0] converged, [1] barrier arrivals, [2] barrier generation, [3] error
+__global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double *__restrict__ V, int m, int maxsweep, int *iw) {
+  const unsigned nb = gridDim.x;
+  unsigned *count = reinterpret_cast<unsigned *>(iw + 1), *gen = reinterpret_cast<unsigned *>(iw + 2);
+  int *err = iw + 3;
+  __shared__ double c_, s_;
+  __shared__ int stop;
+  for (int sweep = 0; sweep < maxsweep; ++sweep) {
+    for (int rd = 0; rd < m - 1; ++rd) {
+      int p, q;
+      jac_pair(m, rd, blockIdx.x, p, q);
+      if (threadIdx.x == 0) {
+        const double app = __ldcg(A + (size_t)p * m + p), aqq = __ldcg(A + (size_t)q * m + q), apq = __ldcg(A + (size_t)p * m + q);
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        c_ = c;
+        s_ = s;
+      }
+      __syncthreads();
+      const double c = c_, s = s_;
+      if (s != 0.0)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+          const double ap = __ldcg(A + (size_t)p * m + k), aq = __ldcg(A + (size_t)q * m + k);
+          __stcg(A + (size_t)p * m + k, c * ap - s * aq);
+          __stcg(A + (size_t)q * m + k, s * ap + c * aq);
+        }
+      if (!grid_barrier(count, gen, nb, err)) return;
+      if (s != 0.0)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+          const double ap = __ldcg(A + (size_t)k * m + p), aq = __ldcg(A + (size_t)k * m + q);
+          __stcg(A + (size_t)k * m + p, c * ap - s * aq);
+          __stcg(A + (size_t)k * m + q, s * ap + c * aq);
+          const double vp = __ldcg(V + (size_t)k * m + p), vq = __ldcg(V + (size_t)k * m + q);
+          __stcg(V + (size_t)k * m + p, c * vp - s * vq);
+          __stcg(V + (size_t)k * m + q, s * vp + c * vq);
+        }
+      if (!grid_barrier(count, gen, nb, err)) return;
+    }
+    if (blockIdx.x == 0) {  // converged when the off-diagonal Frobenius norm is below 1e-15 of the whole
+      double off = 0.0, all = 0.0;
+      for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        const double a = __ldcg(A + t);
+        all += a * a;
+        if (t / m != t % m) off += a * a;
+      }
+      off = block_sum(off);
+      all = block_sum(all);
+      if (threadIdx.x == 0) *(volatile int *)iw = off <= 1e-30 * all ? 1 : 0;
+    }
+    if (!grid_barrier(count, gen, nb, err)) return;
+    if (threadIdx.x == 0) stop = *(volatile int *)iw;
+    __syncthreads();
+    if (stop) break;
+  }
+}
+
+__global__ void k_jac_coop_init(int *iw) {
+  iw[0] = 0;
+  iw[1] = 0;
+  iw[3] = 0;
+}
+
 size_t jacobi_work_doubles(int n) {
   const int m = std::max(2, n + (n & 1));
   return 2 * (size_t)m * m + 2 * (size_t)m;
@@ -1036,6 +1139,21 @@ void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int 
   launch("jac_init", 0, k_jac_init, dim3(std::min(1024, (mm * mm + 255) / 256)), dim3(256), 0, st, Ain, n, A, V, mm, done);
   WDF_CUDA_TRY(cudaGetLastError());
   const int maxsweep = 40;
+  // one cooperative launch when every block of the eigensolve can be resident at once
+  static const bool coop_off = std::getenv("WDF_NO_COOP_JACOBI") != nullptr;
+  int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+  if (!coop_off && cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_coop, 128, 0) == cudaSuccess && coop && mm / 2 <= nsm * per_sm) {
+    launch("jac_init", 0, k_jac_coop_init, dim3(1), dim3(1), 0, st, done);
+    int m_arg = mm, ms_arg = maxsweep;
+    void *args[] = {&A, &V, &m_arg, &ms_arg, &done};
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    WDF_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_jac_coop, dim3(mm / 2), dim3(128), args, 0, st));
+    launch("jac_sort", 0, k_jac_sort, dim3(1), dim3(256), 0, st, A, V, mm, n, w, Vout);
+    WDF_CUDA_TRY(cudaGetLastError());
+    return;
+  }
   int hdone = 0;
   for (int sweep = 0; sweep < maxsweep && !hdone; ++sweep) {
     for (int rd = 0; rd < mm - 1; ++rd) {
