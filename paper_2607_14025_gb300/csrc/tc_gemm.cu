@@ -295,43 +295,62 @@ __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict_
   }
   __syncthreads();
   if (done) {
-    // warp w updates rows w, w + 8, ...: lane l owns values 8 l .. 8 l + 7 of the 256
-    for (int r = warp; r < TM; r += 8) {
-      const int s = s0 + r;
-      if (s >= ny) break;  // rows are in order: the rest of this warp's rows are past the end too
-      float *y = Y + (size_t)s * ldf + f0;
-      const float *p = P ? P + (size_t)s * ldf + f0 : nullptr;
-      float dsum = 0.f;  // a lane adds at most 4 products; the warp sum is FP64
+    // warp w updates rows w, w + 8, ...: lane l owns values 8 l .. 8 l + 7 of the 256. Four rows
+    // at a time: every global load of the four (old Y, P) is issued before their arithmetic and
+    // stores, so they are in flight together
+    constexpr int RB = 4;
+    for (int r0 = warp; r0 < TM; r0 += 8 * RB) {
+      float4 yo[RB][2], pv[RB][2];
 #pragma unroll
-      for (int hq = 0; hq < 2; ++hq) {
-        const int f = 8 * lane + 4 * hq;  // 4 values = 2 complex elements
-        if (f0 + f < kf) {
-          float4 d = *reinterpret_cast<const float4 *>(D + r * DP + f);
-          if (f0 + f + 3 >= kf) d.z = d.w = 0.f;  // one element past the end (kf is even)
-          float4 yv = d;
-          if (c0 != 0.f) {
-            const float4 o = *reinterpret_cast<const float4 *>(y + f);
-            yv = make_float4(fmaf(c0, o.x, d.x), fmaf(c0, o.y, d.y), fmaf(c0, o.z, d.z), fmaf(c0, o.w, d.w));
-          }
-          if (f0 + f + 3 < kf) {
-            *reinterpret_cast<float4 *>(y + f) = yv;
-          } else {
-            *reinterpret_cast<float2 *>(y + f) = make_float2(yv.x, yv.y);
-          }
-          if (p) {
-            const int e = (f0 + f) >> 1;
-            const float4 pv = *reinterpret_cast<const float4 *>(p + f);
-            const float w0 = e < g.len0 ? 1.f : 2.f, w1 = e + 1 < g.len0 ? 1.f : 2.f;
-            dsum += w0 * (pv.x * yv.x + pv.y * yv.y);
-            if (f0 + f + 3 < kf) dsum += w1 * (pv.z * yv.z + pv.w * yv.w);
+      for (int u = 0; u < RB; ++u) {
+        const int s = s0 + r0 + 8 * u;
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+          const int f = 8 * lane + 4 * hq;  // 4 values = 2 complex elements
+          yo[u][hq] = pv[u][hq] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (s < ny && f0 + f < kf) {  // a tail piece reads one element of row padding (kf is even)
+            if (c0 != 0.f) yo[u][hq] = *reinterpret_cast<const float4 *>(Y + (size_t)s * ldf + f0 + f);
+            if (P) pv[u][hq] = *reinterpret_cast<const float4 *>(P + (size_t)s * ldf + f0 + f);
           }
         }
       }
-      if (part) {
-        double dd = (double)dsum;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
-        if (lane == 0) part[(size_t)s * nchunk + blockIdx.y] = dd;
+      for (int u = 0; u < RB; ++u) {
+        const int r = r0 + 8 * u, s = s0 + r;
+        if (s >= ny) break;  // rows are in order: the rest of this warp's rows are past the end too
+        float *y = Y + (size_t)s * ldf + f0;
+        float dsum = 0.f;  // a lane adds at most 4 products; the warp sum is FP64
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+          const int f = 8 * lane + 4 * hq;
+          if (f0 + f < kf) {
+            float4 d = *reinterpret_cast<const float4 *>(D + r * DP + f);
+            if (f0 + f + 3 >= kf) d.z = d.w = 0.f;  // one element past the end
+            float4 yv = d;
+            if (c0 != 0.f) {
+              const float4 o = yo[u][hq];
+              yv = make_float4(fmaf(c0, o.x, d.x), fmaf(c0, o.y, d.y), fmaf(c0, o.z, d.z), fmaf(c0, o.w, d.w));
+            }
+            if (f0 + f + 3 < kf) {
+              *reinterpret_cast<float4 *>(y + f) = yv;
+            } else {
+              *reinterpret_cast<float2 *>(y + f) = make_float2(yv.x, yv.y);
+            }
+            if (P) {
+              const int e = (f0 + f) >> 1;
+              const float4 q4 = pv[u][hq];
+              const float w0 = e < g.len0 ? 1.f : 2.f, w1 = e + 1 < g.len0 ? 1.f : 2.f;
+              dsum += w0 * (q4.x * yv.x + q4.y * yv.y);
+              if (f0 + f + 3 < kf) dsum += w1 * (q4.z * yv.z + q4.w * yv.w);
+            }
+          }
+        }
+        if (part) {
+          double dd = (double)dsum;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+          if (lane == 0) part[(size_t)s * nchunk + blockIdx.y] = dd;
+        }
       }
     }
   }
