@@ -143,12 +143,18 @@ void set_fft_smem_limits(const Geo &g) {
   raise_smem_limit(k_plane<T, OP_ACCUM>, (size_t)(ps));
   set_plane_fast_limits<T>(g);
   set_zpass_fast_limits<T>(g);
+  if constexpr (!std::is_same<T, double>::value) set_zpass_more_limits<T>(g);
 }
+
+// the further compile-time n3 sizes exist for float and double-float
+template <typename T> static constexpr bool has_more() { return !std::is_same<T, double>::value; }
 
 template <typename T>
 void launch_zpass_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st) {
   if (nvec <= 0) return;
   if (zpass_fast_g2r<T>(f, X, nvec, cb, st)) return;
+  if constexpr (has_more<T>())
+    if (zpass_more_g2r<T>(f, X, nvec, cb, st)) return;
   dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
   launch("zpass_g2r", bits_of<T>(), k_zpass_g2r<T, false, 0>, dim3(grid), dim3(kThreads), zpass_smem<T>(f.g), st, X, nvec, f.g, f.P3,
          f.tw3, cb, PDir<T>());
@@ -159,6 +165,8 @@ template <typename T>
 void launch_zpass_g2r_dir(const FftCtx<T> &f, const PDir<T> &d, int nvec, cplx<T> *cb, cudaStream_t st) {
   if (nvec <= 0) return;
   if (zpass_fast_g2r_dir<T>(f, d, nvec, cb, st)) return;
+  if constexpr (has_more<T>())
+    if (zpass_more_g2r_dir<T>(f, d, nvec, cb, st)) return;
   dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
   launch("zpass_g2r", bits_of<T>(), k_zpass_g2r<T, true, 0>, dim3(grid), dim3(kThreads), zpass_smem<T>(f.g), st,
          (const cplx<T> *)d.p, nvec, f.g, f.P3, f.tw3, cb, d);
@@ -169,6 +177,8 @@ template <typename T>
 void launch_zpass_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st) {
   if (nvec <= 0) return;
   if (zpass_fast_r2g<T>(f, epi, cb, nvec, ea, st)) return;
+  if constexpr (has_more<T>())
+    if (zpass_more_r2g<T>(f, epi, cb, nvec, ea, st)) return;
   dim3 grid((nvec + 1) / 2, (f.g.K + kZCols - 1) / kZCols);
   const size_t sm = zpass_smem<T>(f.g);
   if (epi == EPI_STORE) launch("zpass_r2g", bits_of<T>(), k_zpass_r2g<T, EPI_STORE, 0>, dim3(grid), dim3(kThreads), sm, st, cb, nvec, f.g, f.P3, f.tw3, ea);

@@ -53,6 +53,14 @@ template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v);
 bool plane_pipe_available(const Geo &g, const int *err);
 void set_plane_pipe_limits(const Geo &g);
 bool launch_plane_pipe(const FftCtx<float> &f, int npair, const PlaneArgs<float> &pa, cudaStream_t st);
+// compile-time Stockham plane kernels for the further sizes (plane_more_*.cu): float, and
+// double-float in two size groups; false when the size is not in the group
+bool launch_plane_more_f32(const FftCtx<float> &f, int op, int nblk, const PlaneArgs<float> &pa, cudaStream_t st);
+void set_plane_more_limits_f32(const Geo &g);
+bool launch_plane_more_df_a(const FftCtx<df64> &f, int op, int nblk, const PlaneArgs<df64> &pa, cudaStream_t st);
+void set_plane_more_limits_df_a(const Geo &g);
+bool launch_plane_more_df_b(const FftCtx<df64> &f, int op, int nblk, const PlaneArgs<df64> &pa, cudaStream_t st);
+void set_plane_more_limits_df_b(const Geo &g);
 // double-float 64 x 64 plane kernel (plane_df.cu) for OP_VLOC, OP_PROD_R2G and OP_ACCUM
 bool plane_df_available(const Geo &g, const int *jidx);
 void set_plane_df_limits(const Geo &g);
@@ -79,6 +87,12 @@ template <typename T> bool zpass_fast_g2r_dir(const FftCtx<T> &f, const PDir<T> 
 template <typename T>
 bool zpass_fast_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st);
 template <typename T> void set_zpass_fast_limits(const Geo &g);
+// the further sizes (zpass_more_*.cu: float and double-float)
+template <typename T> bool zpass_more_g2r(const FftCtx<T> &f, const cplx<T> *X, int nvec, cplx<T> *cb, cudaStream_t st);
+template <typename T> bool zpass_more_g2r_dir(const FftCtx<T> &f, const PDir<T> &d, int nvec, cplx<T> *cb, cudaStream_t st);
+template <typename T>
+bool zpass_more_r2g(const FftCtx<T> &f, int epi, const cplx<T> *cb, int nvec, const EpiArgs<T> &ea, cudaStream_t st);
+template <typename T> void set_zpass_more_limits(const Geo &g);
 
 // ---------------------------------------------------------------------------------------------
 // dense linear algebra on blocks of internal vectors (rows of length ld, nint live elements)

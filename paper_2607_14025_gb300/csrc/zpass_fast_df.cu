@@ -1,4 +1,5 @@
-// Compile-time n3 transforms, df64 instances (see zpass_fast_impl.cuh).
+// Compile-time n3 transforms for the common sizes, df64 instances (see zpass_fast_impl.cuh).
 #include "zpass_fast_impl.cuh"
 
-WDF_ZFAST_INST(wdf::df64)
+WDF_ZFAST_DEFINE(zpass_fast, WDF_ZFAST_LIST)
+WDF_ZFAST_INSTANTIATE(wdf::df64, zpass_fast)

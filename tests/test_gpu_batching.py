@@ -57,6 +57,27 @@ def test_smallest_batch_system_matches_oracle():
     assert np.abs(outs[0] - ref["out"]).max() <= 1e-8 * np.abs(ref["out"]).max()
 
 
+@pytest.mark.parametrize("index", [1, 3])  # grids 36 (radices 4 3 3) and 45 (5 3 3)
+def test_batch_system_on_further_compile_time_sizes_matches_oracle(index, monkeypatch):
+    # the compile-time Stockham plane kernels and n3 transforms of the further sizes (float inner
+    # iterations, double-float residuals) against the FP64 oracle, each side with its own ground state
+    spec = synth.batch_family(index + 1, seed=0)[index]
+    s = synth.make_system(spec)
+    assert s.grid[0] in (36, 45)
+    H = hamiltonian.Hamiltonian(s)
+    w, psi = H.ground_state(s.nocc)
+    R = dfpt.Response(H, w, psi)
+    phi = synth.make_perturbations(s, 3, 7)
+    ref = R.apply(phi, tol=1e-13)
+    monkeypatch.setenv("WDF_PLANE_VARIANT", "2")  # the compile-time Stockham kernels, whatever the timing
+    with wdf.Context(s, precision="mixed_df", cg_tol=1e-10) as c:
+        assert c.plane_variant(32) == 2 and c.plane_variant(48) == 2
+        out, drho, st = c.apply_chi0(phi, want_drho=True)
+    assert st.converged == 1 and st.max_residual <= 1e-10
+    assert np.abs(drho - ref["drho"]).max() <= 1e-8 * np.abs(ref["drho"]).max()
+    assert np.abs(out - ref["out"]).max() <= 1e-8 * np.abs(ref["out"]).max()
+
+
 def test_multi_rejects_a_repeated_context():
     s = synth.make_system("tiny")
     with wdf.Context(s) as c:
