@@ -404,10 +404,36 @@ void launch_tc_prep_u(const Geo &g, const float2 *U, int na, float *uwh, float *
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
+// K splits of the Gram: one CTA per SM (shared memory), so the launch runs in waves of nsm CTAs;
+// choose the split count (at most nch / 8, so that each CTA keeps a pipeline of >= 8 chunks)
+// that minimises waves x (chunks per CTA + 6), the 6 standing for a CTA's partial-sum write
+// (128 x 192 doubles, about the bytes of a dozen X chunks, written without waiting), the smaller
+// count on ties (fewer partial sums to add)
+static int gram_tc_splits(int nch, int tiles) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
+  }
+  const int smax = std::max(1, std::min(nch / 8, 4 * ((nsm + tiles - 1) / tiles)));
+  long best = -1;
+  int bs = 1;
+  for (int sp = 1; sp <= smax; ++sp) {
+    const long waves = ((long)tiles * sp + nsm - 1) / nsm, per = (nch + sp - 1) / sp;
+    const long cost = waves * (per + 6);
+    if (best < 0 || cost < best) {
+      best = cost;
+      bs = sp;
+    }
+  }
+  return bs;
+}
+
 size_t gram_tc_work_doubles(const Geo &g, int na, int nb) {
   const int nch = (2 * g.nint + TK - 1) / TK;
   const int tiles = (nb + TM - 1) / TM;
-  int nsplit = std::max(1, std::min((2 * 152 + tiles - 1) / tiles, nch / 8));
+  const int nsplit = gram_tc_splits(nch, tiles);
   return nsplit > 1 ? (size_t)nsplit * na * nb : 0;
 }
 
@@ -417,7 +443,7 @@ void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, cons
   const int nu = tc_rows(na);
   const int nch = (2 * g.nint + TK - 1) / TK;
   const int tiles = (nb + TM - 1) / TM;
-  int nsplit = std::max(1, std::min((2 * 152 + tiles - 1) / tiles, nch / 8));
+  int nsplit = gram_tc_splits(nch, tiles);
   if ((size_t)nsplit * na * nb > work_cap) nsplit = 1;
   const int per = (nch + nsplit - 1) / nsplit;
   nsplit = (nch + per - 1) / per;
