@@ -902,6 +902,7 @@ DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nw
   c->dv_Y.ensure(sizeof(double) * (size_t)std::max(nbmax, n0) * std::max(nbmax, n0));
   c->dv_theta.ensure(sizeof(double) * nbmax);
   c->dv_jac.ensure(sizeof(double) * jacobi_work_doubles(nbmax));
+  set_jacobi_limits(nbmax);
   c->dv_jint.ensure(sizeof(int) * 4);
   WDF_CUDA_TRY(cudaMemsetAsync(c->dv_jint.p, 0, sizeof(int) * 4, st));
   c->dv_small.ensure(sizeof(double) * (size_t)std::max(nbmax, n0) * 2);

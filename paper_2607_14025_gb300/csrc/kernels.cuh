@@ -229,5 +229,6 @@ void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc,
 // On exit w holds eigenvalues ascending and V[i * n + k] the i-th component of eigenvector k.
 void jacobi_eigh(double *A, double *V, double *w, int n, double *work, int *iwork, cudaStream_t st);
 size_t jacobi_work_doubles(int n);
+void set_jacobi_limits(int nmax);  // shared memory of the cluster eigensolver for n <= nmax
 
 }  // namespace wdf

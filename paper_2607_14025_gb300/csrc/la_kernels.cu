@@ -1120,25 +1120,197 @@ __global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double
   }
 }
 
+// The eigensolve inside one cluster of kJacCl CTAs (m a multiple of 2 kJacCl, m <= 320): CTA c keeps
+// rows [c R, (c + 1) R) of A and of V in its shared memory (R = m / kJacCl) and reaches the other
+// CTAs' rows through distributed shared memory (mapa / ld,st.shared::cluster). Each round: the
+// CTA that handles pair i (i mod kJacCl) computes (c, s) from A[p][p], A[q][q], A[p][q] and rotates
+// rows p and q wherever they live; cluster barrier; every CTA rotates columns p and q of its own
+// rows of A and V (local); cluster barrier. The hardware cluster barrier replaces the grid
+// barrier's global atomics. Convergence: per-CTA partial sums, read by every CTA after a barrier,
+// the same decision everywhere (the same test as the kernels above).
+constexpr int kJacCl = 8;
+constexpr int kJacThreads = 256;
+constexpr int kJacMaxM = 320;
+
+__device__ __forceinline__ uint32_t cl_addr(const void *local, uint32_t rank) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(local), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double cl_ld(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, double v) { asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory"); }
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// shared memory of one CTA: A rows [R][m], V rows [R][m], (c, s) of its pairs [m / 2][2] (entry i
+// for the pairs i it handles), all pairs' (c, s) [m / 2][2], partial sums [2]
+size_t jac_cluster_smem(int m) {
+  const int R = m / kJacCl;
+  return sizeof(double) * (2 * (size_t)R * m + 2 * (size_t)m + 2);
+}
+
+__global__ void __cluster_dims__(kJacCl, 1, 1) __launch_bounds__(kJacThreads)
+    k_jac_cluster(double *__restrict__ Ag, double *__restrict__ Vg, int m, int maxsweep) {
+  extern __shared__ __align__(16) double jsm[];
+  const int R = m / kJacCl, np = m / 2;
+  double *A = jsm, *V = A + (size_t)R * m, *csown = V + (size_t)R * m, *csall = csown + m, *part = csall + m;
+  const uint32_t me = cl_rank();
+  const int t = threadIdx.x, r0 = (int)me * R;
+  for (int e = t; e < R * m; e += kJacThreads) {
+    const int lr = e / m, k = e % m;
+    A[e] = Ag[(size_t)(r0 + lr) * m + k];
+    V[e] = (r0 + lr == k) ? 1.0 : 0.0;
+  }
+  cl_sync();  // every CTA's rows are in place before any remote access
+  // the local address of row r of A in the CTA that owns it, as a cluster address
+  auto arow = [&](int r) { return cl_addr(A + (size_t)(r % R) * m, (uint32_t)(r / R)); };
+  const int ppc = np / kJacCl;             // pairs handled per CTA and round
+  const int tpp = kJacThreads / ppc;       // threads per handled pair
+  for (int sweep = 0; sweep < maxsweep; ++sweep) {
+    for (int rd = 0; rd < m - 1; ++rd) {
+      // rows: pair i = me + kJacCl * h (h < ppc), handled by threads [h tpp, (h + 1) tpp)
+      {
+        const int h = t / tpp, j = t % tpp, i = (int)me + kJacCl * h;
+        const bool act = h < ppc;  // the threads past ppc tpp have no pair
+        int p = 0, q = 1;
+        if (act) jac_pair(m, rd, i, p, q);
+        const uint32_t ap_row = arow(p), aq_row = arow(q);
+        double app = 0.0, aqq = 0.0, apq = 0.0;
+        if (act) {
+          app = cl_ld(ap_row + 8u * p);
+          aqq = cl_ld(aq_row + 8u * q);
+          apq = cl_ld(ap_row + 8u * q);
+        }
+        double c = 1.0, s = 0.0;
+        if (act && fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+        }
+        if (act && j == 0) {
+          csown[2 * i] = c;
+          csown[2 * i + 1] = s;
+        }
+        __syncthreads();  // the pair's three entries are read before any of its threads rotates them
+        if (act && s != 0.0)
+          for (int k = j; k < m; k += tpp) {
+            const double ap = cl_ld(ap_row + 8u * k), aq = cl_ld(aq_row + 8u * k);
+            cl_st(ap_row + 8u * k, c * ap - s * aq);
+            cl_st(aq_row + 8u * k, s * ap + c * aq);
+          }
+      }
+      cl_sync();
+      // columns: every pair's (c, s) from the CTA that handled it, then the local rows
+      for (int i = t; i < np; i += kJacThreads) {
+        const uint32_t src = cl_addr(csown + 2 * i, (uint32_t)(i % kJacCl));
+        csall[2 * i] = cl_ld(src);
+        csall[2 * i + 1] = cl_ld(src + 8u);
+      }
+      __syncthreads();
+      for (int w = t; w < R * np; w += kJacThreads) {
+        const int lr = w / np, i = w % np;
+        const double c = csall[2 * i], s = csall[2 * i + 1];
+        if (s == 0.0) continue;
+        int p, q;
+        jac_pair(m, rd, i, p, q);
+        double *ar = A + (size_t)lr * m, *vr = V + (size_t)lr * m;
+        const double ap = ar[p], aq = ar[q];
+        ar[p] = c * ap - s * aq;
+        ar[q] = s * ap + c * aq;
+        const double vp = vr[p], vq = vr[q];
+        vr[p] = c * vp - s * vq;
+        vr[q] = s * vp + c * vq;
+      }
+      cl_sync();  // columns done everywhere before the next round reads rows and (c, s)
+    }
+    // convergence: off-diagonal and total squares of the local rows, combined in every CTA
+    double off = 0.0, all = 0.0;
+    for (int e = t; e < R * m; e += kJacThreads) {
+      const double a = A[e];
+      all += a * a;
+      if (r0 + e / m != e % m) off += a * a;
+    }
+    off = block_sum(off);
+    all = block_sum(all);
+    if (t == 0) {
+      part[0] = off;
+      part[1] = all;
+    }
+    cl_sync();
+    __shared__ int stop;
+    if (t == 0) {
+      double o = 0.0, a = 0.0;
+      for (int c = 0; c < kJacCl; ++c) {
+        const uint32_t src = cl_addr(part, (uint32_t)c);
+        o += cl_ld(src);
+        a += cl_ld(src + 8u);
+      }
+      stop = o <= 1e-30 * a ? 1 : 0;
+    }
+    __syncthreads();
+    const bool done = stop != 0;
+    cl_sync();  // every CTA has read the partials before the next sweep overwrites them
+    if (done) break;
+  }
+  for (int e = t; e < R * m; e += kJacThreads) {
+    const int lr = e / m, k = e % m;
+    Ag[(size_t)(r0 + lr) * m + k] = A[e];
+    Vg[(size_t)(r0 + lr) * m + k] = V[e];
+  }
+  cl_sync();  // no CTA leaves while another may still read its shared memory
+}
+
+void set_jacobi_limits(int nmax) {
+  const int m = ((std::max(2, nmax) + 2 * kJacCl - 1) / (2 * kJacCl)) * (2 * kJacCl);
+  if (m <= kJacMaxM) raise_smem_limit(k_jac_cluster, jac_cluster_smem(m));
+}
+
 __global__ void k_jac_coop_init(int *iw) {
   iw[0] = 0;
   iw[1] = 0;
   iw[3] = 0;
 }
 
+// the eigensolver's dimension: n padded to a multiple of 2 kJacCl (zero rows and columns, which
+// no rotation ever mixes in; the sort reads the first n only)
+static int jac_dim(int n) { return ((std::max(2, n) + 2 * kJacCl - 1) / (2 * kJacCl)) * (2 * kJacCl); }
+
 size_t jacobi_work_doubles(int n) {
-  const int m = std::max(2, n + (n & 1));
+  const int m = jac_dim(n);
   return 2 * (size_t)m * m + 2 * (size_t)m;
 }
 
 void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int *iwork, cudaStream_t st) {
   if (n <= 0) return;
-  const int mm = std::max(2, n + (n & 1));
+  const int mm = jac_dim(n);
   double *A = work, *V = work + (size_t)mm * mm, *cs = V + (size_t)mm * mm;
   int *done = iwork;
   launch("jac_init", 0, k_jac_init, dim3(std::min(1024, (mm * mm + 255) / 256)), dim3(256), 0, st, Ain, n, A, V, mm, done);
   WDF_CUDA_TRY(cudaGetLastError());
   const int maxsweep = 40;
+  // one cluster of CTAs with the matrix in distributed shared memory
+  static const bool cluster_off = std::getenv("WDF_NO_CLUSTER_JACOBI") != nullptr;
+  if (!cluster_off && mm <= kJacMaxM) {
+    k_jac_cluster<<<kJacCl, kJacThreads, jac_cluster_smem(mm), st>>>(A, V, mm, maxsweep);
+    if (cudaGetLastError() == cudaSuccess) {
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      launch("jac_sort", 0, k_jac_sort, dim3(1), dim3(256), 0, st, A, V, mm, n, w, Vout);
+      WDF_CUDA_TRY(cudaGetLastError());
+      return;
+    }
+  }
   // one cooperative launch when every block of the eigensolve can be resident at once
   static const bool coop_off = std::getenv("WDF_NO_COOP_JACOBI") != nullptr;
   int dev = 0, coop = 0, nsm = 0, per_sm = 0;
