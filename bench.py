@@ -341,9 +341,9 @@ def run_gpu(args):
     if rank != 0:
         return
     hbm, bf16, src = peaks()
-    # algorithmic flops of the dominant kernel over its timed launches (FFT convention, see
-    # the design doc): per (pair, z plane) block, times the blocks launched (compaction shrinks the
-    # later launches, so the per-launch work varies)
+    # algorithmic flops of the dominant kernel over its timed launches (FFT convention: 5 n log2 n
+    # per complex line): per (pair, z plane) unit, times the units launched (compaction shrinks
+    # the later launches, so the per-launch work varies)
     per_plane_flops = plane_flops(s, 1) / s.grid[2]
     total_flops = per_plane_flops * k_blocks
     avg_ms = k_ms / max(1, k_launches)
