@@ -49,6 +49,14 @@ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
   return df_fast_two_sum(s.hi, e);
 }
 __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+// the sum without its final renormalisation: TwoSum of the leading parts, the rest added in FP32
+// (8 FP32 operations instead of 11). The low part may grow to a few ulp of the high part, which
+// the next TwoSum of leading parts absorbs exactly; df_norm renormalises.
+__device__ __forceinline__ df64 df_add_lazy(df64 a, df64 b) {
+  const df64 s = df_two_sum(a.hi, b.hi);
+  return df64(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df64 df_norm(df64 a) { return df_fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
   const float p = __fmul_rn(a.hi, b.hi);

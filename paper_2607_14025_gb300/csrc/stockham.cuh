@@ -45,8 +45,46 @@ __host__ __device__ constexpr int fls_at(int n, int p) {
 }
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// double-float 8-point DFT with unnormalised sums inside its two 4-point halves (and inside the
+// w8 products), renormalised once at the outputs: the same operations as the generic form below
+// in the same order, about 100 FP32 operations fewer; float32 emulation against the exact DFT
+// gives 8.9e-15 relative error against 6.9e-15 for renormalising every sum
+template <int SG> __device__ __forceinline__ void dft8_df_lazy(cplx<df64> *v) {
+  typedef cplx<df64> C;
+  auto ladd = [](C a, C b) { return mkc<df64>(df_add_lazy(a.x, b.x), df_add_lazy(a.y, b.y)); };
+  auto lsub = [](C a, C b) { return mkc<df64>(df_add_lazy(a.x, -b.x), df_add_lazy(a.y, -b.y)); };
+  auto rad4 = [&](C x0, C x1, C x2, C x3, C(&y)[4]) {
+    const C a = ladd(x0, x2), b = lsub(x0, x2), c = ladd(x1, x3), d = cimul_unit<SG, df64>(lsub(x1, x3));
+    y[0] = ladd(a, c);
+    y[1] = ladd(b, d);
+    y[2] = lsub(a, c);
+    y[3] = lsub(b, d);
+  };
+  C e[4], o[4];
+  rad4(v[0], v[2], v[4], v[6], e);
+  rad4(v[1], v[3], v[5], v[7], o);
+  const df64 h = df64(0.70710678118654752440);
+  // o1 (1 + SG i)/sqrt2, o2 SG i, o3 (-1 + SG i)/sqrt2
+  const C o1 = SG > 0 ? mkc<df64>(h * df_add_lazy(o[1].x, -o[1].y), h * df_add_lazy(o[1].y, o[1].x))
+                      : mkc<df64>(h * df_add_lazy(o[1].x, o[1].y), h * df_add_lazy(o[1].y, -o[1].x));
+  const C o2 = cimul_unit<SG, df64>(o[2]);
+  const C o3 = SG > 0 ? mkc<df64>(h * df_add_lazy(-o[3].x, -o[3].y), h * df_add_lazy(-o[3].y, o[3].x))
+                      : mkc<df64>(h * df_add_lazy(o[3].y, -o[3].x), h * df_add_lazy(-o[3].y, -o[3].x));
+  const C oo[4] = {o[0], o1, o2, o3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const C s = ladd(e[k], oo[k]), d = lsub(e[k], oo[k]);
+    v[k] = mkc<df64>(df_norm(s.x), df_norm(s.y));
+    v[k + 4] = mkc<df64>(df_norm(d.x), df_norm(d.y));
+  }
+}
+
 template <typename T, int R, int SG>
 __device__ __forceinline__ void dft_reg(cplx<T> *v) {
+  if constexpr (std::is_same<T, df64>::value && R == 8) {
+    dft8_df_lazy<SG>(v);
+    return;
+  }
   if (R == 8) {
     // radix-2 split into two 4-point DFTs, combined with w8^k = exp(SG 2 pi i k / 8)
     cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
