@@ -344,8 +344,6 @@ template <typename T> void set_plane_fast_limits(const Geo &g) {
 }
 
 template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nblk, const PlaneArgs<T> &pa, cudaStream_t st) {
-  // the orbital sum of the density response keeps two register blocks across its loop and
-  // spills here; it runs once per chi0 application and stays on the generic kernel
   const int v = op == OP_VLOC ? f.vloc_variant : 0;  // chosen at setup by timing (0: this order)
   if constexpr (std::is_same<T, df64>::value) {
     // the double-float 64 x 64 kernel: V_loc when the setup timing chose it, the product and the
@@ -353,6 +351,9 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
     const bool use = op == OP_VLOC ? v == 6 : (op == OP_PROD_R2G || op == OP_ACCUM);
     if (use && launch_plane_df(f, op, nblk, pa, st)) return true;
   }
+  // the orbital sum of the density response keeps two register blocks across its loop and
+  // spills in the Stockham kernel; it runs once per chi0 application and, outside the 64 x 64
+  // double-float kernel above, stays on the generic kernel
   if (op == OP_ACCUM || f.jidx == nullptr) return false;
   if (v == 3) return false;
   // the other plane operations follow the setup timing of the V_loc product: where the generic
