@@ -11,7 +11,9 @@
 // writes 8 j + r; pass B multiplies element r by w^(r j) (the conjugate in the forward direction),
 // reads and writes j + 8 r. The n1 inverse transform ends with elements j + 8 r of row t % 64 in
 // registers, which is where the product with V_loc (or the orbital sum) happens and where the n1
-// forward transform starts.
+// forward transform starts. The V_loc and product forms fit 64 registers, so two blocks share an
+// SM and one block's barriers do not idle it; the orbital-sum form holds a second register block
+// (the running sum) and runs one block per SM.
 #include <cstdlib>
 
 #include "fft.cuh"
