@@ -44,7 +44,7 @@ enum wdf_status {
   WDF_ENOMEM = 2,   /* device or host allocation failed */
   WDF_ECUDA = 3,    /* CUDA runtime error (message in wdf_last_error) */
   WDF_ENOCONV = 4,  /* an iteration hit its limit; outputs hold the last iterate, stats filled */
-  WDF_ETIMEOUT = 5, /* reserved: a bounded device-side wait expired */
+  WDF_ETIMEOUT = 5, /* a bounded device-side wait expired (the context stays usable) */
   WDF_ENAN = 6,     /* non-finite value in an input or an iterate */
   WDF_ESTATE = 7    /* context unusable after an earlier CUDA failure, or no GPU */
 };
@@ -224,17 +224,18 @@ int wdf_pdep_davidson_seeded(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter
 #define WDF_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 
 /* H x for nvec vectors, the same result as wdf_apply_hamiltonian, without allocating any device
- * memory. For callers that cannot call cudaMalloc: code running inside someone else's CUDA graph
- * capture, processes whose device memory is owned by another allocator (a framework's caching
- * pool), or services with a fixed memory budget. The paper has no counterpart: this entry point
- * only changes where the temporaries live. All of them come from one file-scope device array of
- * WDF_NOALLOC_SCRATCH_BYTES; a call that would need more (about 0.7 MB per vector for a 64^3 grid
- * with 8,440 plane waves) returns WDF_EINVAL and asks for fewer vectors per call.
- * in, out: [nvec][npw_h] complex in DEVICE memory of the context's GPU; out may not alias in.
+ * memory. For callers that cannot call cudaMalloc: processes whose device memory is owned by
+ * another allocator (a framework's caching pool, whose accounting an outside allocation would
+ * break), or services with a fixed device memory budget. The paper has no counterpart: this
+ * entry point only changes where the temporaries live. All of them come from one file-scope
+ * device array of WDF_NOALLOC_SCRATCH_BYTES; a call that would need more (about 0.7 MB per vector
+ * for a 64^3 grid with 8,440 plane waves) returns WDF_EINVAL and asks for fewer vectors per call.
+ * in, out: [nvec][npw_h] complex in DEVICE memory of the context's GPU (checked: anything else
+ * is WDF_EINVAL); out may equal in (the input is read in full before any output is written).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
  * caches it, so make that first call before any stream capture. Every call on a device shares
  * the array: calls whose GPU work may overlap (different streams without ordering) race.
- * Errors: WDF_EINVAL, WDF_ECUDA, WDF_ESTATE. */
+ * Returns after the result is in out. Errors: WDF_EINVAL, WDF_ECUDA, WDF_ESTATE. */
 int wdf_apply_hamiltonian_noalloc(wdf_ctx *ctx, int nvec, const double *in, double *out);
 
 /* ---------------------------------------------------------------------------------------------
@@ -344,6 +345,26 @@ int wdf_plane_variant(const wdf_ctx *ctx, int bits, int *variant);
 
 /* Number of kernel launches the library has made in this process so far (all contexts). */
 int64_t wdf_launch_count(void);
+
+/* Device memory held by the library (no counterpart in the paper: accounting for services that
+ * run under a memory budget). Workspaces are grow-only buffers per context and model.
+ * wdf_device_bytes: bytes those buffers hold now, over all contexts and models of the process
+ *   (the static array behind wdf_apply_hamiltonian_noalloc is not counted).
+ * wdf_alloc_count: cudaMalloc calls the library has made for them so far.
+ * wdf_set_device_limit: cap on the bytes held; a call that would grow a buffer past it returns
+ *   WDF_ENOMEM without allocating, and its context stays usable (a later call with a higher
+ *   cap, or with a smaller block, succeeds). bytes <= 0: no cap (the default). Process-wide. */
+int64_t wdf_device_bytes(void);
+int64_t wdf_alloc_count(void);
+void wdf_set_device_limit(int64_t bytes);
+
+/* Polls a software device wait makes before it gives up: the grid barrier of the cooperative
+ * form of the subspace eigensolver (used when the cluster form is unavailable or disabled with
+ * the environment variable WDF_NO_CLUSTER_JACOBI). On expiry the waiting blocks set the
+ * context's error flag and return, and the call returns WDF_ETIMEOUT with the context still
+ * usable. polls <= 0 restores the default (2^24). For tests of the timeout path and for
+ * callers that prefer an early error to a long stall. Errors: WDF_EINVAL (NULL context). */
+int wdf_set_wait_limit(wdf_ctx *ctx, int64_t polls);
 
 /* Static text for a status code. */
 const char *wdf_strerror(int status);

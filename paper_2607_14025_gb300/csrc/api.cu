@@ -675,6 +675,18 @@ int wdf_plane_variant(const wdf_ctx *c, int bits, int *variant) {
 
 int64_t wdf_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int64_t wdf_device_bytes(void) { return (int64_t)g_dev_bytes.load(); }
+
+int64_t wdf_alloc_count(void) { return (int64_t)g_dev_allocs.load(); }
+
+void wdf_set_device_limit(int64_t bytes) { g_dev_cap.store(bytes > 0 ? (long long)bytes : 0); }
+
+int wdf_set_wait_limit(wdf_ctx *c, int64_t polls) {
+  if (!c) return WDF_EINVAL;
+  c->wait_polls = polls > 0 ? (long)polls : 0;
+  return WDF_OK;
+}
+
 const char *wdf_strerror(int s) {
   switch (s) {
     case WDF_OK: return "success";

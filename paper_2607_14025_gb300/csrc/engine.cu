@@ -925,7 +925,7 @@ DavResult davidson(wdf_ctx *c, DavOp &op, const cplx<double> *V0, int n0, int nw
   for (int it = 1; it <= maxiter; ++it) {
     res.iters = it;
     gram<double>(c, V, nb, W, nb, H, nb);
-    jacobi_eigh(H, Y, theta, nb, c->dv_jac.as<double>(), c->dv_jint.as<int>(), st);
+    jacobi_eigh(H, Y, theta, nb, c->dv_jac.as<double>(), c->dv_jint.as<int>(), st, c->wait_polls);
     const int k = std::min(nkeep, nb);
     launch_lincomb<double>(g, X, k, V, nb, Y, nb, nullptr, 0.0, st);
     launch_lincomb<double>(g, AX, k, W, nb, Y, nb, nullptr, 0.0, st);

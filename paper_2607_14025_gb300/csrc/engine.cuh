@@ -16,6 +16,9 @@ struct DBuf {
   void ensure(size_t bytes);
   void release();
 };
+// device bytes held by all DBufs of the process, cudaMalloc calls made for them, and the cap
+// on the bytes held (0: none); see layout.cu
+extern std::atomic<long long> g_dev_bytes, g_dev_allocs, g_dev_cap;
 
 // Host copy of the plane-wave layout (see layout.cu for its construction).
 struct Layout {
@@ -44,6 +47,7 @@ struct wdf_ctx {
   wdf_options opt{};
   std::string err;
   bool failed = false;
+  long wait_polls = 0;  // wdf_set_wait_limit: polls of software device waits (0: the default)
 
   // system
   int n[3] = {0, 0, 0};

@@ -227,7 +227,10 @@ void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc,
 
 // symmetric eigensolver (cyclic Jacobi, parallel ordering) of an n x n matrix A (ld = n), FP64.
 // On exit w holds eigenvalues ascending and V[i * n + k] the i-th component of eigenvector k.
-void jacobi_eigh(double *A, double *V, double *w, int n, double *work, int *iwork, cudaStream_t st);
+// polls of the cooperative eigensolver's grid barrier before it gives up and flags the error
+constexpr long kGridBarrierPolls = 1L << 24;
+// wait_limit: polls of the cooperative form's grid barrier (<= 0: kGridBarrierPolls)
+void jacobi_eigh(double *A, double *V, double *w, int n, double *work, int *iwork, cudaStream_t st, long wait_limit = 0);
 size_t jacobi_work_doubles(int n);
 void set_jacobi_limits(int nmax);  // shared memory of the cluster eigensolver for n <= nmax
 

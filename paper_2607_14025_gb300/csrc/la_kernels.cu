@@ -1030,9 +1030,7 @@ void set_chol_inv_limits(int nmax) {
 // generation number; a block waits for the bump with a bounded number of polls and, on expiry,
 // sets the error flag and returns (the others then expire at their next barrier). Matrix entries
 // written by other blocks are read past L1 (ld.global.cg), which is not coherent across SMs.
-constexpr long kGridBarrierLimit = 1L << 24;
-
-__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int *err) {
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int *err, long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1046,7 +1044,7 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, i
     } else {
       long it = 0;
       while (*(volatile unsigned *)gen == g0) {
-        if (++it > kGridBarrierLimit) {
+        if (++it > limit) {
           ok = 0;
           atomicExch(err, 1);
           break;
@@ -1060,7 +1058,8 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, i
 }
 
 // iw: [0] converged, [1] barrier arrivals, [2] barrier generation, [3] error
-__global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double *__restrict__ V, int m, int maxsweep, int *iw) {
+__global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double *__restrict__ V, int m, int maxsweep, int *iw,
+                                                  long limit) {
   const unsigned nb = gridDim.x;
   unsigned *count = reinterpret_cast<unsigned *>(iw + 1), *gen = reinterpret_cast<unsigned *>(iw + 2);
   int *err = iw + 3;
@@ -1090,7 +1089,7 @@ __global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double
           __stcg(A + (size_t)p * m + k, c * ap - s * aq);
           __stcg(A + (size_t)q * m + k, s * ap + c * aq);
         }
-      if (!grid_barrier(count, gen, nb, err)) return;
+      if (!grid_barrier(count, gen, nb, err, limit)) return;
       if (s != 0.0)
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
           const double ap = __ldcg(A + (size_t)k * m + p), aq = __ldcg(A + (size_t)k * m + q);
@@ -1100,7 +1099,7 @@ __global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double
           __stcg(V + (size_t)k * m + p, c * vp - s * vq);
           __stcg(V + (size_t)k * m + q, s * vp + c * vq);
         }
-      if (!grid_barrier(count, gen, nb, err)) return;
+      if (!grid_barrier(count, gen, nb, err, limit)) return;
     }
     if (blockIdx.x == 0) {  // converged when the off-diagonal Frobenius norm is below 1e-15 of the whole
       double off = 0.0, all = 0.0;
@@ -1113,7 +1112,7 @@ __global__ void __launch_bounds__(128) k_jac_coop(double *__restrict__ A, double
       all = block_sum(all);
       if (threadIdx.x == 0) *(volatile int *)iw = off <= 1e-30 * all ? 1 : 0;
     }
-    if (!grid_barrier(count, gen, nb, err)) return;
+    if (!grid_barrier(count, gen, nb, err, limit)) return;
     if (threadIdx.x == 0) stop = *(volatile int *)iw;
     __syncthreads();
     if (stop) break;
@@ -1292,7 +1291,7 @@ size_t jacobi_work_doubles(int n) {
   return 2 * (size_t)m * m + 2 * (size_t)m;
 }
 
-void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int *iwork, cudaStream_t st) {
+void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int *iwork, cudaStream_t st, long wait_limit) {
   if (n <= 0) return;
   const int mm = jac_dim(n);
   double *A = work, *V = work + (size_t)mm * mm, *cs = V + (size_t)mm * mm;
@@ -1319,7 +1318,8 @@ void jacobi_eigh(double *Ain, double *Vout, double *w, int n, double *work, int 
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_coop, 128, 0) == cudaSuccess && coop && mm / 2 <= nsm * per_sm) {
     launch("jac_init", 0, k_jac_coop_init, dim3(1), dim3(1), 0, st, done);
     int m_arg = mm, ms_arg = maxsweep;
-    void *args[] = {&A, &V, &m_arg, &ms_arg, &done};
+    long lim_arg = wait_limit > 0 ? wait_limit : kGridBarrierPolls;
+    void *args[] = {&A, &V, &m_arg, &ms_arg, &done, &lim_arg};
     g_launches.fetch_add(1, std::memory_order_relaxed);
     WDF_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_jac_coop, dim3(mm / 2), dim3(128), args, 0, st));
     launch("jac_sort", 0, k_jac_sort, dim3(1), dim3(256), 0, st, A, V, mm, n, w, Vout);

@@ -15,11 +15,23 @@
 
 namespace wdf {
 
+// Device memory held by the library's grow-only buffers (all contexts and models of the
+// process), the cudaMalloc calls made for them, and an optional cap on the bytes held
+// (wdf_set_device_limit; 0: none). A growth the cap refuses leaves the buffer as it was.
+std::atomic<long long> g_dev_bytes{0};
+std::atomic<long long> g_dev_allocs{0};
+std::atomic<long long> g_dev_cap{0};
+
 void DBuf::ensure(size_t bytes) {
   if (bytes <= cap) return;
+  const long long limit = g_dev_cap.load();
+  if (limit > 0 && g_dev_bytes.load() - (long long)cap + (long long)bytes > limit)
+    throw ApiFailure(WDF_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes refused: the library holds " +
+                                     std::to_string(g_dev_bytes.load()) + " of its limit of " + std::to_string(limit) + " bytes");
   if (p) {
     cudaError_t e = cudaFree(p);
     p = nullptr;
+    g_dev_bytes.fetch_sub((long long)cap);
     cap = 0;
     if (e != cudaSuccess) throw CudaFailure(e, "cudaFree", __FILE__, __LINE__);
   }
@@ -30,11 +42,16 @@ void DBuf::ensure(size_t bytes) {
     (void)cudaGetLastError();
     throw ApiFailure(WDF_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   }
+  g_dev_allocs.fetch_add(1);
+  g_dev_bytes.fetch_add((long long)bytes);
   cap = bytes;
 }
 
 void DBuf::release() {
-  if (p) (void)cudaFree(p);
+  if (p) {
+    (void)cudaFree(p);
+    g_dev_bytes.fetch_sub((long long)cap);
+  }
   p = nullptr;
   cap = 0;
 }

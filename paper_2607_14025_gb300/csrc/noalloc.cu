@@ -1,19 +1,20 @@
 // H application for callers that cannot allocate device memory.
 //
-// Some callers of this library run where cudaMalloc is off limits: inside a CUDA graph being
-// captured by someone else, under an allocator that owns all device memory (a framework's caching
-// pool), or in a process whose memory budget is fixed at start-up. For them
-// wdf_apply_hamiltonian_noalloc() computes the same H x as wdf_apply_hamiltonian() but takes every
-// temporary from one file-scope device array of WDF_NOALLOC_SCRATCH_BYTES bytes. That array exists
-// on every GPU that loads the library, for the life of the process. Nothing here calls cudaMalloc,
-// cudaFree or any allocating routine.
+// Some callers of this library run where cudaMalloc is off limits: under an allocator that owns
+// all device memory (a framework's caching pool, which would see its budget broken by an
+// allocation it does not know about), or in a service whose device memory budget is fixed at
+// start-up. For them wdf_apply_hamiltonian_noalloc() computes the same H x as
+// wdf_apply_hamiltonian() but takes every temporary from one file-scope device array of
+// WDF_NOALLOC_SCRATCH_BYTES bytes. That array exists on every GPU that loads the library, for the
+// life of the process. Nothing here calls cudaMalloc, cudaFree or any allocating routine.
 //
 // Host code cannot use the array's name as a device address (in host code it names a host-side
 // stand-in), so the first call on each device looks the address up with cudaGetSymbolAddress
 // while that device is current and caches it; that first call should therefore happen before any
 // stream capture. Every call on a device reuses the same array, which keeps the previous call's
 // contents: the parts that must start at zero are cleared on each call, and two calls whose GPU
-// work overlaps in time (different streams, no ordering) race on the array.
+// work overlaps in time (different streams, no ordering) race on the array. The whole input is
+// copied into the array before the first output element is written, so out may equal in.
 #include <cstring>
 #include <mutex>
 
@@ -41,6 +42,18 @@ static unsigned char *noalloc_base(int device) {
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// the caller's buffers must be device (or managed) memory of the context's GPU
+static void check_device_pointer(const void *p, int device, const char *name) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw ApiFailure(WDF_EINVAL, std::string(name) + " is not a pointer the CUDA runtime knows");
+  }
+  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != device)
+    throw ApiFailure(WDF_EINVAL, std::string(name) + " must point to device memory of the context's GPU");
+}
+
 }  // namespace wdf
 
 using namespace wdf;
@@ -56,6 +69,8 @@ extern "C" int wdf_apply_hamiltonian_noalloc(wdf_ctx *c, int nvec, const double 
     if (nvec == 0) return WDF_OK;
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) throw CudaFailure(e, "cudaSetDevice", __FILE__, __LINE__);
+    check_device_pointer(in, c->device, "in");
+    check_device_pointer(out, c->device, "out");
     const Geo &g = c->geo;
     cudaStream_t st = c->st;
     const int npair = (nvec + 1) / 2;

@@ -157,6 +157,10 @@ def load(path: str = LIB_PATH):
         "wdf_profile_units": (I, [P, P]),
         "wdf_plane_variant": (I, [P, I, ctypes.POINTER(I)]),
         "wdf_launch_count": (ctypes.c_int64, []),
+        "wdf_device_bytes": (ctypes.c_int64, []),
+        "wdf_alloc_count": (ctypes.c_int64, []),
+        "wdf_set_device_limit": (None, [ctypes.c_int64]),
+        "wdf_set_wait_limit": (I, [P, ctypes.c_int64]),
         "wdf_strerror": (ctypes.c_char_p, [I]),
         "wdf_last_error": (ctypes.c_char_p, [P]),
         "wdf_version": (ctypes.c_char_p, []),
@@ -178,6 +182,21 @@ def header_functions(path: str = HEADER):
 def launch_count() -> int:
     """Kernel launches made by the library in this process."""
     return int(load().wdf_launch_count())
+
+
+def device_bytes() -> int:
+    """Device memory held by the library's buffers in this process (wdf_device_bytes)."""
+    return int(load().wdf_device_bytes())
+
+
+def alloc_count() -> int:
+    """cudaMalloc calls the library has made in this process (wdf_alloc_count)."""
+    return int(load().wdf_alloc_count())
+
+
+def set_device_limit(nbytes: int) -> None:
+    """Cap the device memory the library may hold (0: no cap); growth past it is WDF_ENOMEM."""
+    load().wdf_set_device_limit(int(nbytes))
 
 
 # ------------------------------------------------------------------------------------------------
@@ -322,18 +341,31 @@ class Context:
     def apply_hamiltonian_noalloc(self, x, out):
         """H x into ``out`` without any device allocation by the library.
 
-        For callers that cannot allocate GPU memory (inside another component's graph capture,
-        or under an allocator that owns the device): x and out are complex128 CUDA tensors of
-        shape (nvec, npw_h) that the caller owns; the library's temporaries live in a fixed
-        64 MiB device array. The first call on a device must come before any stream capture.
+        For callers that cannot allocate GPU memory (a process whose device memory belongs to
+        another allocator, or a service with a fixed memory budget): x and out are complex128
+        CUDA tensors of shape (nvec, npw_h) on the context's GPU that the caller owns; ``out``
+        may be ``x`` itself. The library's temporaries live in a fixed 64 MiB device array. The
+        first call on a device must come before any stream capture.
         """
-        if not (_is_torch(x) and x.is_cuda and _is_torch(out) and out.is_cuda):
-            raise TypeError("apply_hamiltonian_noalloc takes CUDA tensors for x and out")
-        xs = x.contiguous()
-        if not out.is_contiguous() or out.shape != xs.shape or out.dtype != xs.dtype:
-            raise ValueError("out must be a contiguous tensor shaped like x")
-        self._check(self._lib.wdf_apply_hamiltonian_noalloc(self._ctx, xs.shape[0], xs.data_ptr(), out.data_ptr()))
+        import torch
+
+        for name, t in (("x", x), ("out", out)):
+            if not (_is_torch(t) and t.is_cuda):
+                raise TypeError(f"apply_hamiltonian_noalloc takes CUDA tensors; {name} is not one")
+            if t.dtype != torch.complex128 or t.ndim != 2 or t.shape[1] != self.npw_h:
+                raise ValueError(f"{name} must be complex128 of shape (nvec, {self.npw_h}), got {t.dtype} {tuple(t.shape)}")
+            if t.device.index != self.device:
+                raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{self.device}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+        if out.shape != x.shape:
+            raise ValueError("out must have the shape of x")
+        self._check(self._lib.wdf_apply_hamiltonian_noalloc(self._ctx, x.shape[0], x.data_ptr(), out.data_ptr()))
         return out
+
+    def set_wait_limit(self, polls: int):
+        """Polls of the software device waits before they give up (wdf_set_wait_limit; 0: default)."""
+        self._check(self._lib.wdf_set_wait_limit(self._ctx, int(polls)))
 
     def sternheimer(self, vidx, rhs):
         keep: list = []

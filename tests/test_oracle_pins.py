@@ -237,6 +237,16 @@ def test_tpa_limits():
     assert abs(k[2] * 2 * x[2] - 1.0) < 2e-5  # K = (1 + 1/x + ...) / (2x)
 
 
+def test_tpa_interior_values_by_hand():
+    # Teter, Payne and Allan's polynomial P = 27 + 18x + 12x^2 + 8x^3 evaluated by hand:
+    # x = 1/2: P = 27 + 9 + 3 + 1 = 40, 16 x^4 = 1   -> K = 40/41
+    # x = 1:   P = 27 + 18 + 12 + 8 = 65, 16 x^4 = 16 -> K = 65/81
+    # x = 2:   P = 27 + 36 + 48 + 64 = 175, 16 x^4 = 256 -> K = 175/431
+    # (each coefficient enters at a different weight, so a wrong one fails at least one value)
+    k = dfpt.tpa(np.array([0.5, 1.0, 2.0]))
+    assert np.abs(k - np.array([40 / 41, 65 / 81, 175 / 431])).max() < 1e-15
+
+
 # ---------------------------------------------------------------------------------------------
 # PDEP
 
