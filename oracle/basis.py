@@ -18,7 +18,10 @@ import os
 import numpy as np
 import scipy.fft
 
-_WORKERS = max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
+# FFT threads: every core the process may use, unless ORACLE_FFT_WORKERS says otherwise (a pool of
+# oracle processes gives each a share)
+_WORKERS = int(os.environ.get("ORACLE_FFT_WORKERS", "0")) or max(
+    1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
 
 
 def full_miller(miller_half: np.ndarray) -> np.ndarray:

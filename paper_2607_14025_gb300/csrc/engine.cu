@@ -1048,7 +1048,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   int bestv = 0;
   if (const char *pin = std::getenv("WDF_PLANE_VARIANT")) {  // fixed choice, e.g. to compare contexts bit for bit
     const int v = std::atoi(pin);
-    if (v >= 1 && v <= 6 && plane_variant_available<T>(f, v)) {
+    if (v >= 1 && v <= kPlaneVariants && plane_variant_available<T>(f, v)) {
       f.vloc_variant = v;
       cbuf.release();
       return;
@@ -1057,7 +1057,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   try {
     WDF_CUDA_TRY(cudaEventCreate(&e0));
     WDF_CUDA_TRY(cudaEventCreate(&e1));
-    for (int v = 1; v <= 6; ++v) {
+    for (int v = 1; v <= kPlaneVariants; ++v) {
       if (!plane_variant_available<T>(f, v)) continue;
       f.vloc_variant = v;
       launch_plane<T>(f, OP_VLOC, nblk, pa, st);  // warm-up
@@ -1084,7 +1084,7 @@ template <typename T> static void autotune_vloc(wdf_ctx *c, FftCtx<T> &f, const 
   cbuf.release();
   f.vloc_variant = bestv;
   if (std::getenv("WDF_TRACE"))
-    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic, 4 two-thread register, 5 persistent, 6 double-float), %.3f ms per %d pairs\n",
+    fprintf(stderr, "[wdf] V_loc plane kernel (%d-bit): variant %d (1 register, 2 Stockham, 3 generic, 4 two-thread register, 5 persistent, 6 double-float, 7 two-thread persistent), %.3f ms per %d pairs\n",
             bits_of<T>(), bestv, best / 3, nblk);
 }
 
@@ -1131,12 +1131,13 @@ void finish_setup(wdf_ctx *c) {
   // FP32 copy of the projectors and orbitals
   c->U32.ensure(sizeof(cplx<float>) * (size_t)M * g.ld);
   launch_convert<double, float>(g, (float *)c->U32.p, (const double *)c->U64.p, 2 * (size_t)M * g.ld, st);
-  // tensor-core copies of U for the FP32 projections (at most 256 rows fit one MMA)
+  // tensor-core copies of U for the FP32 projections (the Gram runs in chunks of 256 rows of U, the
+  // linear combination in K chunks of 32, so any height up to kTcMaxRows)
   // one device flag for every kernel with a bounded wait (tensor-core MMAs, bulk copies)
   c->tcerr.ensure(sizeof(int));
   WDF_CUDA_TRY(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), st));
   c->f32.err = c->tcerr.as<int>();
-  c->tc_on = tc_enabled() && M >= 1 && M <= 256;
+  c->tc_on = tc_enabled() && M >= 1 && M <= kTcMaxRows;
   if (c->tc_on) {
     const int kp = tc_rows(M);
     c->tcU.ensure(sizeof(float) * 2 * (size_t)M * 2 * g.ld);

@@ -20,7 +20,8 @@ template <typename T> struct FftCtx {
   int vloc_variant = 0;            // V_loc plane kernel: 0 default order, 1 register, 2 Stockham, 3 generic,
                                    // 4 register with two threads per line (n1 = n2 = 64), 5 persistent
                                    // with bulk copies (64 x 64 planes with a full disk), 6 double-float
-                                   // one task per thread (64 x 64)
+                                   // one task per thread (64 x 64), 7 persistent with two threads per
+                                   // line (96 x 96 planes with a full disk)
   int *err = nullptr;              // device flag set by a kernel whose bounded wait expired
 };
 
@@ -49,10 +50,15 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
 // whether V_loc plane variant v (1 register, 2 Stockham, 3 generic, 4 two-thread register,
 // 5 persistent with bulk copies, 6 double-float one task per thread) exists
 template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v);
+constexpr int kPlaneVariants = 7;  // variants are numbered 1 .. kPlaneVariants
 // persistent FP32 V_loc plane kernel (plane_pipe.cu); false when the geometry has no instance
 bool plane_pipe_available(const Geo &g, const int *err);
 void set_plane_pipe_limits(const Geo &g);
 bool launch_plane_pipe(const FftCtx<float> &f, int npair, const PlaneArgs<float> &pa, cudaStream_t st);
+// persistent FP32 V_loc plane kernel with two threads per line (plane_pipe2.cu; 96 x 96 planes)
+bool plane_pipe2_available(const Geo &g, const int *err);
+void set_plane_pipe2_limits(const Geo &g);
+bool launch_plane_pipe2(const FftCtx<float> &f, int npair, const PlaneArgs<float> &pa, cudaStream_t st);
 // compile-time Stockham plane kernels for the further sizes (plane_more_*.cu): float, and
 // double-float in two size groups; false when the size is not in the group
 bool launch_plane_more_f32(const FftCtx<float> &f, int op, int nblk, const PlaneArgs<float> &pa, cudaStream_t st);
@@ -217,6 +223,8 @@ bool tc_enabled();
 int tc_rows(int na);  // rows of U rounded up to 32 (the MMA N of the projections, <= 256)
 void set_tc_limits();
 void launch_tc_prep_u(const Geo &g, const float2 *U, int na, float *uwh, float *uwl, float *uth, float *utl, cudaStream_t st);
+// most rows of U ([beta; psi]) the tensor-core projections take (memory of the hi/lo copies only)
+constexpr int kTcMaxRows = 4096;
 size_t gram_tc_work_doubles(const Geo &g, int na, int nb);
 // out[j][s] (ldo = nb) = sum_e w_e Re(conj(U_j) X_s) for j < na, s < nb
 void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, const float *uwl, int na, double *out, double *work,

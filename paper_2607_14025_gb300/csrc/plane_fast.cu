@@ -327,6 +327,7 @@ template <typename T> void set_plane_fast_limits(const Geo &g) {
   if (std::is_same<T, float>::value && g.n1 == g.n2) {
     set_plane_reg_limits(g);
     set_plane_pipe_limits(g);
+    set_plane_pipe2_limits(g);
   }
   if (std::is_same<T, df64>::value) set_plane_df_limits(g);
   if constexpr (std::is_same<T, float>::value) set_plane_more_limits_f32(g);
@@ -361,6 +362,7 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
   if (op != OP_VLOC && f.vloc_variant == 3) return false;
   if constexpr (std::is_same<T, float>::value) {
     if (op == OP_VLOC && v == 5 && launch_plane_pipe(f, nblk, pa, st)) return true;
+    if (op == OP_VLOC && v == 7 && launch_plane_pipe2(f, nblk, pa, st)) return true;
     if (op == OP_VLOC && v == 4 && launch_plane_reg2(f, nblk, pa, st)) return true;
     if (op == OP_VLOC && v != 2 && launch_plane_reg(f, nblk, pa, st)) return true;
   }
@@ -384,6 +386,7 @@ template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v) {
   if (f.jidx == nullptr) return false;
   if (v == 4) return std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == 64 && g.n2 == 64;
   if (v == 5) return std::is_same<T, float>::value && plane_pipe_available(g, f.err);
+  if (v == 7) return std::is_same<T, float>::value && plane_pipe2_available(g, f.err);
   if (v == 6) return std::is_same<T, df64>::value && plane_df_available(g, f.jidx);
   if (v == 2) return plane_fast_supported(g.n1, g.n2) || (!std::is_same<T, double>::value && plane_more_supported(g.n1, g.n2));
   if (v == 1 && std::is_same<T, float>::value && reg_plane_enabled() && g.n1 == g.n2) {

@@ -79,10 +79,54 @@ template <int SG> __device__ __forceinline__ void dft8_df_lazy(cplx<df64> *v) {
   }
 }
 
+// modular inverse of a modulo m (a and m coprime, small): the smallest x >= 1 with a x = 1 mod m
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+  int x = 1;
+  while ((a * x) % m != 1) ++x;
+  return x;
+}
+
+// R = A B point DFT with A and B coprime by the prime-factor (Good-Thomas) map: input n =
+// (B n1 + A n2) mod R, output k = (B (B^-1 mod A) k1 + A (A^-1 mod B) k2) mod R, so that
+// w_R^(n k) = w_A^(n1 k1) w_B^(n2 k2) and no twiddle factors are needed.
+template <typename T, int A, int B, int SG>
+__device__ __forceinline__ void dft_pfa(cplx<T> *v) {
+  constexpr int R = A * B;
+  constexpr int cA = B * inv_mod(B % A, A), cB = A * inv_mod(A % B, B);
+  cplx<T> a[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2)
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) a[n2][n1] = v[(B * n1 + A * n2) % R];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) small_dft<T, SG>(a[n2], A);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    cplx<T> b[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) b[n2] = a[n2][k1];
+    small_dft<T, SG>(b, B);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[(cA * k1 + cB * k2) % R] = b[k2];
+  }
+}
+
 template <typename T, int R, int SG>
 __device__ __forceinline__ void dft_reg(cplx<T> *v) {
   if constexpr (std::is_same<T, df64>::value && R == 8) {
     dft8_df_lazy<SG>(v);
+    return;
+  }
+  if constexpr (R == 6) {
+    dft_pfa<T, 3, 2, SG>(v);
+    return;
+  }
+  if constexpr (R == 10) {
+    dft_pfa<T, 5, 2, SG>(v);
+    return;
+  }
+  if constexpr (R == 12) {
+    dft_pfa<T, 3, 4, SG>(v);
     return;
   }
   if (R == 8) {

@@ -48,12 +48,21 @@ __device__ __forceinline__ float4 load_masked(const float *row, int f, int kf) {
 // i + 1 are loaded into registers while the MMAs of chunk i run, so global latency overlaps them.
 constexpr int UPT = 8;  // U pieces per thread and operand part at most (256 rows x 8 pieces / 256 threads)
 
+// blockIdx.z picks a chunk of at most kGramRows rows of U (rows z kGramRows ...): a CTA holds the
+// accumulators of 128 solves x one chunk in TMEM, so U of any height runs in chunks.
+constexpr int kGramRows = 256;
+
 __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restrict__ X, int nb, const float *__restrict__ Uhi,
-                                                    const float *__restrict__ Ulo, int na, int nu, double *__restrict__ out, int ldo,
+                                                    const float *__restrict__ Ulo, int na_all, double *__restrict__ out, int ldo,
                                                     int ch_per_split, size_t split_stride, int *__restrict__ err) {
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = align1024(smraw);
-  const int UB = nu * 128, SB = 2 * XB + 2 * UB;
+  const int j0 = blockIdx.z * kGramRows;
+  const int na = min(kGramRows, na_all - j0), nu = ((na + 31) / 32) * 32;
+  Uhi += (size_t)j0 * 2 * g.ld;
+  Ulo += (size_t)j0 * 2 * g.ld;
+  out += (size_t)j0 * ldo;
+  const int UB = nu * 128, SB = 2 * XB + 2 * UB;  // the launch sizes shared memory for the largest chunk
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * SB);
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + 2 * SB + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -432,7 +441,7 @@ static int gram_tc_splits(int nch, int tiles) {
 
 size_t gram_tc_work_doubles(const Geo &g, int na, int nb) {
   const int nch = (2 * g.nint + TK - 1) / TK;
-  const int tiles = (nb + TM - 1) / TM;
+  const int tiles = ((nb + TM - 1) / TM) * ((na + kGramRows - 1) / kGramRows);
   const int nsplit = gram_tc_splits(nch, tiles);
   return nsplit > 1 ? (size_t)nsplit * na * nb : 0;
 }
@@ -440,19 +449,20 @@ size_t gram_tc_work_doubles(const Geo &g, int na, int nb) {
 void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, const float *uwl, int na, double *out, double *work,
                     size_t work_cap, int *err, cudaStream_t st) {
   if (nb <= 0 || na <= 0) return;
-  const int nu = tc_rows(na);
+  const int nmc = (na + kGramRows - 1) / kGramRows;
+  const int nu = tc_rows(std::min(na, kGramRows));
   const int nch = (2 * g.nint + TK - 1) / TK;
   const int tiles = (nb + TM - 1) / TM;
-  int nsplit = gram_tc_splits(nch, tiles);
+  int nsplit = gram_tc_splits(nch, tiles * nmc);
   if ((size_t)nsplit * na * nb > work_cap) nsplit = 1;
   const int per = (nch + nsplit - 1) / nsplit;
   nsplit = (nch + per - 1) / per;
   if (nsplit == 1) {
-    launch("gram", 32, k_gram_tc, dim3(tiles, 1), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, nu, out, nb, per, (size_t)0,
+    launch("gram", 32, k_gram_tc, dim3(tiles, 1, nmc), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, out, nb, per, (size_t)0,
            err);
   } else {
     const size_t stride = (size_t)na * nb;
-    launch("gram", 32, k_gram_tc, dim3(tiles, nsplit), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, nu, work, nb, per,
+    launch("gram", 32, k_gram_tc, dim3(tiles, nsplit, nmc), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, work, nb, per,
            stride, err);
     WDF_CUDA_TRY(cudaGetLastError());
     launch("gram_sum", 0, k_tc_sum_splits, dim3((unsigned)(((size_t)na * nb + 255) / 256)), dim3(256), 0, st, (const double *)work,

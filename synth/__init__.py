@@ -48,6 +48,8 @@ __all__ = [
     "SPECS",
     "BATCH_GRIDS",
     "batch_family",
+    "GRID_SIZES",
+    "grid_probe",
     "spec",
     "make_system",
     "make_perturbations",
@@ -131,6 +133,10 @@ SPECS = {
     "ragged": SystemSpec("ragged", 11.0, (30, 30, 30), 16.0, 3, 6, 8.0, 1.0, 0.8, -2.0, 5.0, 3.0, 2),
     "medium": SystemSpec("medium", 20.0, (64, 64, 64), 25.0, 32, 64, 12.0, 1.0, 0.8, -2.0, 5.0, 5.0, 0),
     "precision": SystemSpec("precision", 28.0, (96, 96, 96), 25.0, 128, 256, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, 0),
+    # the precision system's cell, grid, cutoff and plane-wave layout (23,149 stored waves, the
+    # same compile-time kernels) with 8 atoms and 16 orbitals, so that the oracle finishes in
+    # about a minute
+    "precision_reduced": SystemSpec("precision_reduced", 28.0, (96, 96, 96), 25.0, 8, 16, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, 0),
 }
 
 
@@ -151,6 +157,17 @@ def batch_family(count: int = 16, seed: int = 0) -> list:
         out.append(SystemSpec(f"batch{k}", L, (n, n, n), 25.0, natom, 2 * natom, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5,
                               1000 * seed + k))
     return out
+
+
+# Every FFT grid size the library has compile-time kernels for (n3 transforms and plane kernels);
+# grid_probe(n) is a cheap system on each: the precision family's spacing, cutoff, wells and
+# projectors (L = 28 n / 96 bohr, |G|^2 <= 25), two atoms and four occupied orbitals.
+GRID_SIZES = (24, 30, 32, 36, 40, 45, 48, 50, 54, 60, 64, 72, 75, 80, 96)
+
+
+def grid_probe(n: int, seed: int = 7) -> SystemSpec:
+    """Spec of the two-atom system on an n^3 grid (deterministic in ``seed``)."""
+    return SystemSpec(f"grid{n}", n * 28.0 / 96.0, (n, n, n), 25.0, 2, 4, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, seed)
 
 
 def spec(name: str) -> SystemSpec:

@@ -1,20 +1,27 @@
-"""Precision form on the large configuration (L = 28 bohr, 96^3 grid, 23,149 stored plane waves,
-128 atoms, 512 projectors, 256 occupied orbitals) through the C ABI.
+"""Precision forms on the 96^3 grid of the precision configuration (L = 28 bohr, |G|^2 <= 25,
+23,149 stored plane waves) through the C ABI.
 
-The FP64 oracle would need hours here, so the per-result errors of the reduced-precision forms
-are measured against the plain FP64 GPU form (itself held to the oracle at 1e-8 on the tiny,
-small and ragged systems), on the same orbitals and perturbations, and the FP64 result is checked
-for properties of chi0bar that hold at any size: symmetry and negative semidefiniteness of
-<phi_a, chi0bar phi_b>, and a density response without G = 0 component.
-Bar: 1e-8 relative (largest deviation over the largest magnitude) at cg_tol 1e-10, the same as
-the mixed forms' parity bar against the oracle.
+* Against the oracle: the reduced precision system (same cell, grid, cutoff and plane-wave
+  layout, hence the same compile-time kernels and tile shapes, but 8 atoms, 32 projectors and 16
+  occupied orbitals so that the FP64 oracle finishes in about a minute). Every precision form is
+  compared element by element with the oracle on drho and chi0bar phi: the plain FP64 form at
+  cg_tol 1e-12 and the mixed forms at cg_tol 1e-10, all held to 1e-8 relative (largest deviation
+  over the largest magnitude). The measured errors are written to the file named by the
+  environment variable WDF_PARITY_REPORT when it is set.
+* The full precision system (128 atoms, 512 projectors, 256 occupied orbitals), where the oracle
+  would need hours: properties of chi0bar that hold at any size on the FP64 result (symmetry and
+  negative semidefiniteness of <phi_a, chi0bar phi_b>, no G = 0 density component), and, as an
+  extra check, the mixed forms against the FP64 form.
 """
+
+import json
+import os
 
 import numpy as np
 import pytest
 
 import synth
-from oracle import basis
+from oracle import basis, dfpt, hamiltonian
 
 pytestmark = pytest.mark.gpu
 
@@ -23,6 +30,37 @@ wdf = pytest.importorskip("paper_2607_14025_gb300.wdf")
 
 def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+@pytest.fixture(scope="module")
+def reduced():
+    from paper_2607_14025_gb300 import build
+
+    build.build()
+    s = synth.make_system("precision_reduced")
+    H = hamiltonian.Hamiltonian(s)
+    w, psi = H.ground_state(s.nocc + 2, tol=1e-11)
+    R = dfpt.Response(H, w[: s.nocc], psi[: s.nocc])
+    phi = synth.make_perturbations(s, 3, 41)
+    ref = R.apply(phi, tol=1e-13)
+    return s, phi, ref
+
+
+@pytest.mark.parametrize("prec,cg_tol", [("fp64", 1e-12), ("mixed", 1e-10), ("mixed_df", 1e-10)])
+def test_reduced_precision_system_matches_oracle(reduced, prec, cg_tol):
+    s, phi, ref = reduced
+    assert s.npw_h == 23149 and tuple(s.grid) == (96, 96, 96)
+    with wdf.Context(s, precision=prec, cg_tol=cg_tol, gs_tol=1e-11) as c:
+        out, drho, st = c.apply_chi0(phi, want_drho=True)
+    assert st.converged == 1 and st.max_residual <= cg_tol
+    e_drho, e_out = rel(drho, ref["drho"]), rel(out, ref["out"])
+    path = os.environ.get("WDF_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"system": "precision_reduced", "precision": prec, "cg_tol": cg_tol, "drho_rel_err": e_drho,
+                                "out_rel_err": e_out, "max_residual": st.max_residual}) + "\n")
+    assert e_drho <= 1e-8, prec
+    assert e_out <= 1e-8, prec
 
 
 @pytest.fixture(scope="module")
