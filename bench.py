@@ -1,17 +1,24 @@
 """Benchmark: Sternheimer solves/s and chi0bar applications/s at 1e-8 residual on one GB300.
 
-Workload (the medium configuration): cubic cell L = 20 bohr, FFT grid 64^3, plane-wave cutoff
-|G|^2 <= 25 bohr^-2 (16,879 plane waves, 8,440 stored at Gamma), 32 Gaussian-well atoms with s and
-p Kleinman-Bylander projectors (128 projectors), 64 occupied orbitals (computed by the library),
-128 orthonormal seeded perturbations. One step is one pass of the whole hot path over that block:
-wdf_pdep_davidson with one iteration, i.e. v^1/2, dV in real space, right-hand sides, the
-64 x 128 = 8,192 Sternheimer solves to ||b - A x|| <= 1e-8 ||b||, the density response, v^1/2 and
-the Rayleigh-Ritz step of PDEP (subspace matrix, FP64 eigensolve, Ritz residuals).
+Workload (the precision configuration, the largest that fits one GPU): cubic cell L = 28 bohr,
+FFT grid 96^3, plane-wave cutoff |G|^2 <= 25 bohr^-2 (46,297 plane waves, 23,149 stored at
+Gamma), 128 Gaussian-well atoms with s and p Kleinman-Bylander projectors (512 projectors), 256
+occupied orbitals (computed by the library), a block of 512 orthonormal seeded perturbations.
+The block is applied in 8 chunks of 64 (a whole block of 512 x 256 solves would need ~800 GB of
+CG workspace); one step is one pass of the whole hot path over one chunk: wdf_pdep_davidson for
+64 eigenpairs with one iteration, i.e. v^1/2, dV in real space, right-hand sides, the
+64 x 256 = 16,384 Sternheimer solves to ||b - A x|| <= 1e-8 ||b||, the density response, v^1/2
+and the Rayleigh-Ritz step of PDEP (subspace matrix, FP64 eigensolve, Ritz residuals). Steps
+cycle through the chunks, so 8 steps cover the 512-perturbation block.
+
+Beside it, in the same line: the plain FP64 GPU form on a sample of the same block (the
+metric's "vs FP64 GPU"), the medium configuration (64^3, 64 orbitals, 128 perturbations per
+step) as a secondary figure, and the FP64 CPU oracle on a bounded sample (cpu_baseline).
 
 Timing: W warm-up steps, then K steps bracketed by barriers and device synchronisation, CUDA events
 on the library's stream; L2 is flushed (256 MiB write) before every step and the step's working
-set (~10 GB) exceeds L2 anyway. The e2e figure repeats the step through the same C ABI with host
-buffers (host-to-device copy of the perturbations and device-to-host copy of the eigenpairs
+set (~100 GB) exceeds L2 anyway. The e2e figure repeats the steps through the same C ABI with
+host buffers (host-to-device copy of the perturbations and device-to-host copy of the eigenpairs
 inside the timed region). Multi-GPU: the path shards by perturbation blocks with no exchange, so
 each rank runs its own block (weak scaling) and rank 0 reports the total.
 
@@ -37,13 +44,35 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-WORKLOAD = "medium"
-NPERT = 128
-NEIG = 64
 METRIC = "sternheimer_solves_per_s_at_1e-8"
-# the workload both arms report in config.workload (the reference arm times a bounded sample of it)
-WORKLOAD_DESC = ("medium: L=20 bohr, 64^3 grid, |G|^2<=25, 8440 stored PWs, 32 atoms (128 KB projectors), "
-                 "64 occupied, 128 perturbations per GPU, PDEP 64 eigenpairs, one Davidson iteration per step")
+UNIT = "solves/s"
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    system: str      # synth spec
+    nblock: int      # perturbations of the block per GPU
+    chunk: int       # perturbations per step (one Davidson iteration of PDEP on them)
+    neig: int        # PDEP eigenpairs
+    desc: str        # config.workload of the JSON line
+    oracle_system: str  # system the CPU oracle is timed on
+    oracle_nv: int   # Sternheimer solves (orbitals of one perturbation) per oracle sample
+
+
+WORKLOADS = {
+    "precision": Workload(
+        "precision", 512, 64, 64,
+        "precision: L=28 bohr, 96^3 grid, |G|^2<=25, 23149 stored PWs, 128 atoms (512 KB projectors), 256 occupied, "
+        "512 perturbations per GPU applied in 8 chunks of 64; one step = one chunk: PDEP 64 eigenpairs, one Davidson "
+        "iteration (16384 solves)",
+        "precision_reduced", 8),
+    "medium": Workload(
+        "medium", 128, 128, 64,
+        "medium: L=20 bohr, 64^3 grid, |G|^2<=25, 8440 stored PWs, 32 atoms (128 KB projectors), 64 occupied, "
+        "128 perturbations per GPU, PDEP 64 eigenpairs, one Davidson iteration per step",
+        "medium", 64),
+}
+
 # kernel class timed for the roofline, per precision: (class, bound). The per-plane FFT kernel
 # keeps its data on chip (its HBM traffic is the column buffer only): its limit is arithmetic.
 ROOFLINE_KERNEL = {"mixed_df": ("plane_vloc:32", "alu"), "mixed": ("plane_vloc:32", "alu"), "fp64": ("plane_vloc:64", "alu")}
@@ -55,14 +84,14 @@ ALU_PEAK_SOURCE = {"mixed_df": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (d
                    "fp64": "FP64: measured FMA loop on GB300, 1.19 TFLOP/s"}
 
 
-# DRAM bytes per (pair, z plane) unit of the FP32 V_loc plane kernel on the medium system, per
-# kernel variant (the one chosen at setup, wdf_plane_variant), from one ncu capture each
+# DRAM bytes per (pair, z plane) unit of the FP32 V_loc plane kernel, per (grid, kernel variant
+# chosen at setup), from one ncu capture each on a small case of the same system
 # (dram__bytes_read.sum + dram__bytes_write.sum over the units of the captured launch; see
 # profiles/); traffic grows in proportion to the units launched. A variant without a capture of
 # its current code reports null.
-PLANE64_DRAM_BYTES_PER_UNIT = {
-    1: (210.873088e6 + 167.385088e6) / 32768,  # k_plane_reg<64>: 32,768 units
-    5: (210.877440e6 + 149.595648e6) / 32768,  # k_plane_pipe<15>: 32,768 units
+PLANE_DRAM_BYTES_PER_UNIT = {
+    (64, 1): (210.873088e6 + 167.385088e6) / 32768,  # k_plane_reg<64>: 32,768 units
+    (64, 5): (210.877440e6 + 149.595648e6) / 32768,  # k_plane_pipe<15>: 32,768 units
 }
 
 
@@ -80,7 +109,6 @@ def plane_flops(system, npair: int) -> float:
     line = lambda n: 5.0 * n * math.log2(n)  # noqa: E731
     per_plane = 2.0 * (nx * line(n2) + n2 * line(n1)) + 2.0 * n1 * n2
     return per_plane * n3 * npair
-UNIT = "solves/s"
 
 
 def peaks():
@@ -138,18 +166,45 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(system_name: str, nsolve_target: int = 64):
-    """Time the FP64 oracle on one perturbation (all occupied orbitals) of the workload."""
-    from oracle import dfpt, hamiltonian
+class OracleSample:
+    """The FP64 CPU oracle on a bounded sample of a workload: its own ground state (not timed),
+    then, per timed sample, one perturbation's right-hand sides for the first ``nv`` occupied
+    orbitals (Q over all of them), their Sternheimer solves to 1e-8 and their density."""
 
-    s = synth.make_system(system_name)
-    H = hamiltonian.Hamiltonian(s)
-    t0 = time.time()
-    w, psi = H.ground_state(s.nocc, tol=1e-6)
-    t_gs = time.time() - t0
-    R = dfpt.Response(H, w, psi)
-    phi = synth.make_perturbations(s, 1, 0)
-    return s, R, phi, t_gs
+    def __init__(self, wl: Workload):
+        from oracle import dfpt, hamiltonian
+
+        self.wl = wl
+        self.s = synth.make_system(wl.oracle_system)
+        H = hamiltonian.Hamiltonian(self.s)
+        t0 = time.time()
+        w, psi = H.ground_state(self.s.nocc, tol=1e-8)
+        self.t_gs = time.time() - t0
+        self.R = dfpt.Response(H, w, psi)
+        self.nv = min(wl.oracle_nv, self.s.nocc)
+        self.x = self.R.vhalf_times(synth.make_perturbations(self.s, 1, 0))
+
+    def run(self):
+        """One sample; returns (seconds, solves, mean CG iterations)."""
+        vidx = np.arange(self.nv)
+        pidx = np.zeros(self.nv, dtype=np.int64)
+        t0 = time.time()
+        b = self.R.rhs(self.x[pidx], vidx)
+        d, iters, _ = self.R.sternheimer(b, vidx, tol=1e-8)
+        self.R.density(d, vidx, 1, pidx)
+        return time.time() - t0, self.nv, float(np.mean(iters))
+
+    def describe(self) -> str:
+        s = self.s
+        same = self.wl.oracle_system == self.wl.system
+        what = (f"1 perturbation x {self.nv} of {s.nocc} occupied orbitals (Q over all {s.nocc}) = {self.nv} Sternheimer "
+                f"solves at 1e-8 with their right-hand sides and density, FP64 numpy/scipy oracle")
+        if same:
+            return what + f" (oracle ground state {self.t_gs:.0f} s, not timed)"
+        return (what + f", on {s.spec.name}: the workload's {s.grid[0]}^3 grid and {s.npw_h}-wave basis with "
+                f"{s.spec.natom} atoms and {s.nocc} orbitals, since the oracle's ground state of the full system would take "
+                f"hours; its solves project on {s.nocc} instead of 256 orbitals and {s.nproj} instead of 512 projectors, so "
+                f"the rate overstates the oracle on the full system (ground state {self.t_gs:.0f} s, not timed)")
 
 
 def rank_block_seed(rank: int) -> int:
@@ -181,33 +236,56 @@ def cores():
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on a bounded sample, one perturbation per step."""
+    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload, one sample per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    s, R, phi, t_gs = oracle_sample(WORKLOAD)
-    times = []
-    nsolve = s.nocc
+    wl = WORKLOADS.get(args.workload, WORKLOADS["medium"])
+    o = OracleSample(wl)
+    times, its = [], []
     for i in range(args.warmup + args.steps):
-        t0 = time.time()
-        o = R.apply(phi, tol=1e-8)
-        dt = time.time() - t0
+        dt, nsolve, it = o.run()
         if i >= args.warmup:
             times.append(dt)
+            its.append(it)
     ms = 1e3 * sum(times) / len(times)
-    value = nsolve / (ms * 1e-3)
+    value = o.nv / (ms * 1e-3)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": "fp64 (CPU oracle)", "cg_tol": 1e-8,
-                   "sample": "1 perturbation (all occupied orbitals) per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle",
-                         "sample": f"1 perturbation x {nsolve} occupied orbitals = {nsolve} Sternheimer solves per step (FP64 numpy/scipy oracle)"},
+        "config": {"workload": wl.desc, "precision": "fp64 (CPU oracle)", "cg_tol": 1e-8,
+                   "sample": f"{o.nv} solves per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle", "sample": o.describe()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "cg_iters_per_solve": float(np.mean(o["iters"])),
+        "cg_iters_per_solve": float(np.mean(its)),
     }
     print(json.dumps(line), flush=True)
+
+
+def roofline_line(s, precision, variant, k_launches, k_ms, k_blocks, steps, ms_dev):
+    """The dominant kernel's roofline from its live CUDA-event timing inside the timed region."""
+    target, bound = ROOFLINE_KERNEL[precision]
+    # algorithmic flops of the kernel over its timed launches (FFT convention: 5 n log2 n per
+    # complex line): per (pair, z plane) unit, times the units launched (compaction shrinks the
+    # later launches, so the per-launch work varies)
+    per_plane_flops = plane_flops(s, 1) / s.grid[2]
+    total_flops = per_plane_flops * k_blocks
+    avg_ms = k_ms / max(1, k_launches)
+    achieved = total_flops / (k_ms * 1e-3) / 1e12 if k_launches else None
+    alu_peak = ALU_PEAK_TFLOPS[precision]
+    # algorithmic bytes: the column-buffer slice read and written (8 B per disk column and z)
+    blocks_per_launch = k_blocks / max(1, k_launches)
+    full = np.concatenate([s.miller, -s.miller[1:]])
+    ndisk = len({(int(a), int(b)) for a, b, _ in full})
+    alg_bytes = blocks_per_launch * 2 * ndisk * 8
+    per_unit = PLANE_DRAM_BYTES_PER_UNIT.get((s.grid[0], variant)) if precision != "fp64" else None
+    return {"kernel": target, "variant": variant, "bound": bound, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": (achieved / alu_peak) if achieved else None, "traffic": per_unit * blocks_per_launch if per_unit else None,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "algorithmic_bytes_per_launch": alg_bytes,
+            "launches_per_step": k_launches / steps, "ms_per_launch": avg_ms, "share_of_step": k_ms / steps / ms_dev,
+            "algorithmic_flops_per_launch": total_flops / max(1, k_launches), "flops_per_pair_plane": per_plane_flops,
+            "pair_planes_per_step": k_blocks / steps, "peak_source": ALU_PEAK_SOURCE[precision]}
 
 
 def run_gpu(args):
@@ -227,60 +305,66 @@ def run_gpu(args):
         wbuild.build()
     if world > 1:
         dist.barrier()
+    wl = WORKLOADS[args.workload]
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    s = synth.make_system(WORKLOAD)
+    s = synth.make_system(wl.system)
     # each rank applies chi0bar to its own seeded perturbation block (weak scaling)
-    phi_h = synth.make_perturbations(s, NPERT, rank_block_seed(rank))
+    phi_h = synth.make_perturbations(s, wl.nblock, rank_block_seed(rank))
+    nch = wl.nblock // wl.chunk
     t_setup = time.perf_counter()
     ctx = wdf.Context(s, precision=args.precision, cg_tol=1e-8, stream=stream.cuda_stream, device=local,
                       max_batch=args.max_batch)
     t_setup = time.perf_counter() - t_setup
-    eps, _ = ctx.orbitals()
+    eps, psi = ctx.orbitals()
+
     def train_learned():
         # train on other seeds of the same system family (the benchmarked system is seed 0)
         t_tr = time.perf_counter()
-        fam = [wdf.Context(synth.make_system(dataclasses.replace(synth.spec(WORKLOAD), seed=k)), precision=args.precision, cg_tol=1e-8,
-                           stream=stream.cuda_stream, device=local) for k in range(1, args.train_systems + 1)]
+        fam = [wdf.Context(synth.make_system(dataclasses.replace(synth.spec(wl.system), seed=k)), precision=args.precision,
+                           cg_tol=1e-8, stream=stream.cuda_stream, device=local) for k in range(1, args.train_systems + 1)]
         model, ts = wdf.train_preconditioner(fam, npert=args.train_npert, steps=args.train_steps, seed=12345)
         for c in fam:
             c.close()
         ctx.set_model(model)
-        return {"systems": f"{WORKLOAD} family, seeds 1..{args.train_systems} (benchmarked system: seed 0)",
+        return {"systems": f"{wl.system} family, seeds 1..{args.train_systems} (benchmarked system: seed 0)",
                 "perturbations_per_system": args.train_npert, "samples": ts.nsamples, "adam_steps": ts.steps,
                 "loss_first": ts.loss_first, "loss_last": ts.loss_last, "train_ms": ts.ms,
                 "wall_s_incl_ground_states": time.perf_counter() - t_tr}
 
     train_info = train_learned() if args.precond == "learned" else None
     phi_d = torch.from_numpy(phi_h).to(dev)
+    chunks_d = [phi_d[k * wl.chunk:(k + 1) * wl.chunk] for k in range(nch)]
+    chunks_h = [np.ascontiguousarray(phi_h[k * wl.chunk:(k + 1) * wl.chunk]) for k in range(nch)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(phi):
         try:
-            return ctx.pdep(NEIG, phi, maxiter=1, tol=1e-8)
-        except wdf.NotConverged as e:  # one Davidson iteration never converges all 64 pairs
+            return ctx.pdep(wl.neig, phi, maxiter=1, tol=1e-8)
+        except wdf.NotConverged as e:  # one Davidson iteration never converges every pair
             return e.result
 
     if args.profile_step:
         # one warm step, then exactly one step inside cudaProfilerStart/Stop (for ncu
         # --profile-from-start off); prints a short summary and exits
         with torch.cuda.stream(stream):
-            step(phi_d)
+            step(chunks_d[0])
             torch.cuda.synchronize(dev)
             torch.cuda.profiler.start()
-            lam, vec, st = step(phi_d)
+            lam, vec, st = step(chunks_d[0])
             torch.cuda.synchronize(dev)
             torch.cuda.profiler.stop()
-        print(json.dumps({"profile_step": True, "npert": NPERT, "precision": args.precision, "stats": st.as_dict()}))
+        print(json.dumps({"profile_step": True, "workload": args.workload, "chunk": wl.chunk, "precision": args.precision,
+                          "stats": st.as_dict()}))
         ctx.close()
         return
 
     # dominant kernel of the step, timed live with CUDA events on its stream
     target, bound = ROOFLINE_KERNEL[args.precision]
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for i in range(args.warmup):
             flush.fill_(1.0)
-            step(phi_d)
+            step(chunks_d[i % nch])
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
@@ -293,7 +377,7 @@ def run_gpu(args):
         for i in range(args.steps):
             flush.fill_(1.0)
             ev[i][0].record(stream)
-            lam, vec, st = step(phi_d)
+            lam, vec, st = step(chunks_d[i % nch])
             ev[i][1].record(stream)
             stats.append(st.as_dict())
         torch.cuda.synchronize(dev)
@@ -304,27 +388,28 @@ def run_gpu(args):
         variant = ctx.plane_variant(32 if args.precision != "fp64" else 64)  # plane kernel chosen at setup
         ctx.profile_kernel(None)
         ms_dev = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-        # end to end through the C ABI with host buffers
+        # end to end through the C ABI with host buffers: one pass over the block's chunks
+        n_e2e = max(1, min(args.steps, nch))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            lam_h, vec_h, st_h = step(phi_h)
+        for i in range(n_e2e):
+            lam_h, vec_h, st_h = step(chunks_h[i % nch])
         torch.cuda.synchronize(dev)
-        ms_e2e = 1e3 * (time.perf_counter() - t0) / args.steps
+        ms_e2e = 1e3 * (time.perf_counter() - t0) / n_e2e
     learned_line = None
-    if args.precond == "tpa" and args.with_learned and world == 1:
+    if args.precond == "tpa" and args.with_learned and wl.system == "medium" and world == 1:
         # the same step with the learned preconditioner (trained here, not timed), same protocol
         info = train_learned()
         with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
+            for i in range(args.warmup):
                 flush.fill_(1.0)
-                step(phi_d)
+                step(chunks_d[i % nch])
             torch.cuda.synchronize(dev)
             evl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
             for i in range(args.steps):
                 flush.fill_(1.0)
                 evl[i][0].record(stream)
-                _, _, stl = step(phi_d)
+                _, _, stl = step(chunks_d[i % nch])
                 evl[i][1].record(stream)
             torch.cuda.synchronize(dev)
         ms_l = sum(a.elapsed_time(b) for a, b in evl) / args.steps
@@ -332,75 +417,182 @@ def run_gpu(args):
         learned_line = {"value": job_throughput(world, dl["nsolve"], ms_l), "unit": UNIT, "ms_per_step": ms_l,
                         "cg_iters_per_solve": dl["cg_iters"] / max(1, dl["nsolve"]), "cg_iters_max": dl["cg_iters_max"],
                         "max_residual": dl["max_residual"], "fallbacks_per_step": dl["fallbacks"], "training": info}
+    ctx.close()
+    fp64_line = None
+    if args.fp64_npert > 0:
+        # the plain FP64 GPU form on a sample of the same block (same orbitals, same CG tolerance)
+        with wdf.Context(s, psi=psi, eps=eps, precision="fp64", cg_tol=1e-8, stream=stream.cuda_stream, device=local) as c64:
+            sample = chunks_d[0][: args.fp64_npert]
+            with torch.cuda.stream(stream):
+                c64.apply_chi0(sample)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 2
+                e0.record(stream)
+                for _ in range(reps):
+                    _, _, st64 = c64.apply_chi0(sample)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+            ms64 = e0.elapsed_time(e1) / reps
+            d64 = st64.as_dict()
+        fp64_line = {"value": job_throughput(world, d64["nsolve"], ms64), "unit": UNIT, "ms_per_call": ms64,
+                     "sample": f"{args.fp64_npert} perturbations x {s.nocc} orbitals = {d64['nsolve']} solves of the same block, "
+                               "chi0bar applications (S1-S8) in plain FP64 on the GPU, cg_tol 1e-8, CUDA events, 1 warm-up + 2 timed",
+                     "cg_iters_per_solve": d64["cg_iters"] / max(1, d64["nsolve"]), "max_residual": d64["max_residual"]}
     ms_dev, ms_e2e = reduce_step_times([ms_dev, ms_e2e], device=dev)
     nsolve = stats[-1]["nsolve"]
     iters = stats[-1]["cg_iters"] / max(1, nsolve)
     value = job_throughput(world, nsolve, ms_dev)
     e2e = job_throughput(world, nsolve, ms_e2e)
-    ctx.close()
+    secondary = None
+    if args.secondary and wl.system != "medium" and world == 1:
+        secondary = run_secondary_medium(args, stream, dev, flush)
     if rank != 0:
         return
     hbm, bf16, src = peaks()
-    # algorithmic flops of the dominant kernel over its timed launches (FFT convention: 5 n log2 n
-    # per complex line): per (pair, z plane) unit, times the units launched (compaction shrinks
-    # the later launches, so the per-launch work varies)
-    per_plane_flops = plane_flops(s, 1) / s.grid[2]
-    total_flops = per_plane_flops * k_blocks
-    avg_ms = k_ms / max(1, k_launches)
-    per_launch_flops = total_flops / max(1, k_launches)
-    achieved = total_flops / (k_ms * 1e-3) / 1e12 if k_launches else None
-    alu_peak = ALU_PEAK_TFLOPS[args.precision]
-    # DRAM traffic per launch from the ncu capture (FP32 64^3 kernel only), and the algorithmic
-    # bytes: the column-buffer slice read and written (8 B per disk column and z) + V_loc plane
-    blocks_per_launch = k_blocks / max(1, k_launches)
-    full = np.concatenate([s.miller, -s.miller[1:]])
-    ndisk = len({(int(a), int(b)) for a, b, _ in full})
-    alg_bytes = blocks_per_launch * 2 * ndisk * 8
-    per_unit = PLANE64_DRAM_BYTES_PER_UNIT.get(variant) if args.precision != "fp64" and tuple(s.grid) == (64, 64, 64) else None
-    traffic = per_unit * blocks_per_launch if per_unit else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed": "f32+f64", "mixed_df": "f32+df64+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "precond": args.precond, "cg_tol": 1e-8,
+        "config": {"workload": wl.desc, "precision": args.precision, "precond": args.precond, "cg_tol": 1e-8,
                    "l2": "flushed (256 MiB write) before each step; working set > L2",
                    "parallelism": f"perturbation blocks x{world}"},
-        "chi0_applies_per_s": job_throughput(world, NPERT, ms_dev),
+        "chi0_applies_per_s": job_throughput(world, wl.chunk, ms_dev),
         "cg_iters_per_solve": iters,
         "cg_iters_max": stats[-1]["cg_iters_max"],
         "max_residual": stats[-1]["max_residual"],
         "fallbacks_per_step": stats[-1]["fallbacks"],
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": NPERT * s.npw_h * 16,
-                "d2h_bytes_per_step": NEIG * s.npw_h * 16 + NEIG * 8},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": wl.chunk * s.npw_h * 16,
+                "d2h_bytes_per_step": wl.neig * s.npw_h * 16 + wl.neig * 8, "steps": n_e2e},
         "gpu_launches": int(round(launches)),
-        "roofline": {"kernel": target, "variant": variant, "bound": bound, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
-                     "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "launches_per_step": k_launches / args.steps, "ms_per_launch": avg_ms,
-                     "share_of_step": k_ms / args.steps / ms_dev, "algorithmic_flops_per_launch": per_launch_flops,
-                     "flops_per_pair_plane": per_plane_flops, "pair_planes_per_step": k_blocks / args.steps,
-                     "peak_source": ALU_PEAK_SOURCE[args.precision]},
+        "roofline": roofline_line(s, args.precision, variant, k_launches, k_ms, k_blocks, args.steps, ms_dev),
         "clocks": clocks,
         "peaks_source": src,
         "setup_s": t_setup,
         "eps_homo": float(eps[-1]),
     }
+    if fp64_line:
+        line["fp64_gpu"] = fp64_line
+        line["mixed_over_fp64_gpu"] = value / fp64_line["value"]
+    if secondary:
+        line["medium"] = secondary
     if train_info:
         line["learned_preconditioner"] = train_info
     if learned_line:
         line["learned_preconditioner"] = learned_line
     if args.cpu_baseline:
-        sys_o, R, phi1, t_gs = oracle_sample(WORKLOAD)
-        t0 = time.time()
-        o = R.apply(phi1, tol=1e-8)
-        dt = time.time() - t0
-        line["cpu_baseline"] = {"value": sys_o.nocc / dt, "unit": UNIT, "cores": cores(), "kind": "oracle",
-                                "sample": f"1 perturbation x {sys_o.nocc} occupied = {sys_o.nocc} Sternheimer solves at 1e-8 "
-                                          f"(ground state by the oracle's iterative eigensolver, {t_gs:.0f} s, not timed)"}
+        o = OracleSample(wl)
+        dt, nv, it = o.run()
+        line["cpu_baseline"] = {"value": nv / dt, "unit": UNIT, "cores": cores(), "kind": "oracle", "sample": o.describe()}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_secondary_medium(args, stream, dev, flush):
+    """The medium configuration with the same step (PDEP, one Davidson iteration over 128
+    perturbations), a few steps, as a secondary figure of the line."""
+    import torch
+
+    from paper_2607_14025_gb300 import wdf
+
+    wl = WORKLOADS["medium"]
+    s = synth.make_system(wl.system)
+    phi = torch.from_numpy(synth.make_perturbations(s, wl.nblock, rank_block_seed(0))).to(dev)
+    with wdf.Context(s, precision=args.precision, cg_tol=1e-8, stream=stream.cuda_stream, device=dev.index) as c:
+        def step():
+            try:
+                return c.pdep(wl.neig, phi, maxiter=1, tol=1e-8)
+            except wdf.NotConverged as e:
+                return e.result
+
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                flush.fill_(1.0)
+                step()
+            n = 5
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+            for i in range(n):
+                flush.fill_(1.0)
+                ev[i][0].record(stream)
+                _, _, st = step()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / n
+    d = st.as_dict()
+    return {"workload": wl.desc, "value": d["nsolve"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": n, "warmup": 2,
+            "cg_iters_per_solve": d["cg_iters"] / max(1, d["nsolve"]), "max_residual": d["max_residual"]}
+
+
+def run_learned(args):
+    """The learned-preconditioner protocol: a model trained on converged solves of 32 seeded
+    systems of the family (96^3 and 128^3 grids alternating, L = 28 n / 96 bohr, |G|^2 <= 25, the
+    reduced precision system's atom density) is applied to 8 held-out seeds; each held-out system
+    applies chi0bar to a block of perturbations to 1e-8 with TPA and with the learned scale.
+    Reports CG iterations per solve, wall time (CUDA events, one warm-up apply each) and the TPA
+    fallbacks."""
+    import torch
+
+    from paper_2607_14025_gb300 import build as wbuild
+    from paper_2607_14025_gb300 import wdf
+
+    torch.cuda.set_device(0)
+    wbuild.build()
+    grids = (96, 128)
+    t0 = time.perf_counter()
+    train = [wdf.Context(synth.make_system(synth.learned_family(k, grids[k % 2])), precision=args.precision, cg_tol=1e-8)
+             for k in range(args.learned_train)]
+    t_gs = time.perf_counter() - t0
+    model, ts = wdf.train_preconditioner(train, npert=args.train_npert, steps=args.train_steps, seed=12345)
+    for c in train:
+        c.close()
+    rows = []
+    tot = {"tpa": [0, 0.0, 0], "learned": [0, 0.0, 0]}  # solves, ms, iterations
+    fallbacks = 0
+    for k in range(args.learned_train, args.learned_train + args.learned_test):
+        s = synth.make_system(synth.learned_family(k, grids[k % 2]))
+        phi = torch.from_numpy(synth.make_perturbations(s, args.learned_npert, 700 + k)).cuda()
+        row = {"seed": k, "grid": s.grid[0], "nocc": s.nocc, "npw_h": s.npw_h}
+        with wdf.Context(s, precision=args.precision, cg_tol=1e-8) as c:
+            for name in ("tpa", "learned"):
+                c.set_model(model if name == "learned" else None)
+                c.apply_chi0(phi)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _, _, st = c.apply_chi0(phi)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                d = st.as_dict()
+                row[name] = {"cg_iters_per_solve": d["cg_iters"] / d["nsolve"], "ms": ms, "max_residual": d["max_residual"],
+                             "fallbacks": d["fallbacks"]}
+                tot[name][0] += d["nsolve"]
+                tot[name][1] += ms
+                tot[name][2] += d["cg_iters"]
+                if name == "learned":
+                    fallbacks += d["fallbacks"]
+        rows.append(row)
+    value = tot["learned"][0] / (tot["learned"][1] * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": tot["learned"][1], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "mixed_df": "f32+df64+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": f"learned: train seeds 0..{args.learned_train - 1}, held-out seeds {args.learned_train}.."
+                               f"{args.learned_train + args.learned_test - 1}, grids 96^3/128^3 alternating, "
+                               f"{args.learned_npert} perturbations per held-out system, cg_tol 1e-8",
+                   "precision": args.precision},
+        "tpa": {"value": tot["tpa"][0] / (tot["tpa"][1] * 1e-3), "unit": UNIT, "ms": tot["tpa"][1],
+                "cg_iters_per_solve": tot["tpa"][2] / tot["tpa"][0]},
+        "learned": {"value": value, "unit": UNIT, "ms": tot["learned"][1], "cg_iters_per_solve": tot["learned"][2] / tot["learned"][0],
+                    "fallbacks": fallbacks},
+        "iteration_gain": tot["tpa"][2] / max(1, tot["learned"][2]),
+        "time_gain": tot["tpa"][1] / tot["learned"][1],
+        "training": {"systems": args.learned_train, "samples": ts.nsamples, "adam_steps": ts.steps, "loss_first": ts.loss_first,
+                     "loss_last": ts.loss_last, "train_ms": ts.ms, "ground_states_s": t_gs},
+        "systems": rows,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_batching(args):
@@ -475,26 +667,32 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true", help="one warm step, then one step between "
                     "cudaProfilerStart/Stop for ncu --profile-from-start off; no timing line")
-    ap.add_argument("--npert", type=int, default=128, help="perturbations per block (default 128)")
     ap.add_argument("--precond", choices=["tpa", "learned"], default="tpa",
                     help="learned: train the MLP preconditioner on other seeds of the family first (not timed)")
     ap.add_argument("--no-learned", dest="with_learned", action="store_false",
                     help="skip the extra timing of the learned preconditioner after the TPA headline")
-    ap.add_argument("--workload", choices=["medium", "batching"], default="medium",
-                    help="batching: the uneven multi-system workload (its own line; medium is the headline)")
+    ap.add_argument("--workload", choices=["precision", "medium", "batching", "learned"], default="precision",
+                    help="precision (the headline: 96^3, 256 orbitals, 512 perturbations in chunks of 64); medium "
+                         "(64^3, 64 orbitals, 128 perturbations); batching: the uneven multi-system workload (its own line)")
+    ap.add_argument("--fp64-npert", type=int, default=2,
+                    help="perturbations of the block timed in the plain FP64 GPU form (0: skip)")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the secondary medium-configuration figure")
+    ap.add_argument("--learned-train", type=int, default=32, help="learned workload: training seeds")
+    ap.add_argument("--learned-test", type=int, default=8, help="learned workload: held-out seeds")
+    ap.add_argument("--learned-npert", type=int, default=32, help="learned workload: perturbations per held-out system")
     ap.add_argument("--batch-systems", type=int, default=16)
     ap.add_argument("--batch-npert", type=int, default=64)
     ap.add_argument("--train-systems", type=int, default=4)
     ap.add_argument("--train-npert", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=600)
     args = ap.parse_args()
-    global NPERT, NEIG
-    NPERT = args.npert
-    NEIG = min(NEIG, NPERT)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batching":
         run_batching(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

@@ -22,6 +22,9 @@ constexpr int TM = 128;              // MMA M: solves per tile
 constexpr int TK = 32;               // K values per stage (one 128-byte row)
 constexpr int XB = TM * 128;         // bytes of a 128-row operand tile
 constexpr long kWaitLimit = 1L << 26;  // polls of an mbarrier before giving up
+// chunks per FP32 accumulation chain of the Gram: longer chains lose accuracy (the sums run over
+// 2 N_int products), so every kPromote chunks the partial sums move into the FP64 output
+constexpr int kPromote = 32;
 
 __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
   return (unsigned char *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
@@ -76,12 +79,35 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
     tc::mbar_init(&bar[1], 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(slot, 256);
+  if (warp == 0) tc::tmem_alloc(slot, 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
   const uint32_t idesc = tc::idesc_tf32(TM, nu);
+  // accumulation chains of kPromote chunks alternate between the two TMEM halves; a finished
+  // chain is added into the FP64 output while the next one accumulates in the other half
+  const int qd = warp & 3, hh = warp >> 2, orow = 32 * qd + lane, osol = s0 + orow;
+  double *o = out + (size_t)blockIdx.y * split_stride;
+  auto promote = [&](int p) {  // the first chain stores, later chains add
+    tc::fence_after_sync();
+    const uint32_t base = tmem + (uint32_t)((p & 1) * 256);
+    const int halfc = nu / 2;
+    for (int cg = 0; cg < halfc; cg += 16) {
+      const int col = hh * halfc + cg;
+      float v[16];
+      tc::tmem_ld16(base + ((uint32_t)(32 * qd) << 16) + (uint32_t)col, v);
+      if (osol < nb)
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (col + k < na) {
+            double *d = o + (size_t)(col + k) * ldo + osol;
+            *d = p == 0 ? (double)v[k] : *d + (double)v[k];
+          }
+    }
+    tc::fence_before_sync();
+  };
+  int promoted = 0;
   float4 rx[4], rh[UPT], rl[UPT];
   auto fetch = [&](int c) {
     const int f0 = c * TK;
@@ -108,6 +134,10 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
     unsigned char *S = sm + st * SB;
     if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
     if (!ok) break;
+    if (i >= 2 && (i - 2) % kPromote == kPromote - 1) {  // chunk i - 2 closed a chain: its MMAs are done
+      promote((i - 2) / kPromote);
+      promoted = (i - 2) / kPromote + 1;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int t = tid + 256 * u;
@@ -127,12 +157,14 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
     if (tid == 0) {
       tc::fence_after_sync();
       const uint32_t base = tc::smem_u32(S);
+      const uint32_t acc = tmem + (uint32_t)(((i / kPromote) & 1) * 256);
+      const int first = i % kPromote;
 #pragma unroll
       for (int term = 0; term < 3; ++term) {
         const uint32_t a = base + (term == 2 ? XB : 0), b = base + 2 * XB + (term == 1 ? UB : 0);
 #pragma unroll
         for (int ks = 0; ks < TK / 8; ++ks)
-          tc::mma_tf32(tmem, tc::desc_sw128(a + 32 * ks), tc::desc_sw128(b + 32 * ks), idesc, (i | term | ks) ? 1u : 0u);
+          tc::mma_tf32(acc, tc::desc_sw128(a + 32 * ks), tc::desc_sw128(b + 32 * ks), idesc, (first | term | ks) ? 1u : 0u);
       }
       tc::mma_commit(&bar[st]);
     }
@@ -143,25 +175,17 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
   bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
   done = __syncthreads_and(done) && ok && issued == c1 - c0;
   if (done) {
-    tc::fence_after_sync();
-    const int qd = warp & 3, h = warp >> 2, row = 32 * qd + lane, s = s0 + row;
-    double *o = out + (size_t)blockIdx.y * split_stride;
-    const int half = nu / 2;
-    for (int cg = 0; cg < half; cg += 16) {
-      const int col = h * half + cg;
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)col, v);
-      if (s < nb)
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (col + k < na) o[(size_t)(col + k) * ldo + s] = (double)v[k];
+    if (issued == 0) {  // an empty K range still owns its part of the output
+      if (osol < nb)
+        for (int col = hh * (nu / 2); col < (hh + 1) * (nu / 2) && col < na; ++col) o[(size_t)col * ldo + osol] = 0.0;
     }
+    for (int p = promoted; p * kPromote < issued; ++p) promote(p);  // the chains still in TMEM (at most two)
   } else if (tid == 0) {
     atomicExch(err, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 __global__ void k_tc_sum_splits(const double *__restrict__ work, int nsplit, size_t stride, double *__restrict__ out, int na, int nb,

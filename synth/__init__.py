@@ -50,6 +50,7 @@ __all__ = [
     "batch_family",
     "GRID_SIZES",
     "grid_probe",
+    "learned_family",
     "spec",
     "make_system",
     "make_perturbations",
@@ -168,6 +169,15 @@ GRID_SIZES = (24, 30, 32, 36, 40, 45, 48, 50, 54, 60, 64, 72, 75, 80, 96)
 def grid_probe(n: int, seed: int = 7) -> SystemSpec:
     """Spec of the two-atom system on an n^3 grid (deterministic in ``seed``)."""
     return SystemSpec(f"grid{n}", n * 28.0 / 96.0, (n, n, n), 25.0, 2, 4, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, seed)
+
+
+def learned_family(seed: int, n: int = 96) -> SystemSpec:
+    """A member of the learned-preconditioner family: the precision system's spacing, cutoff,
+    wells and projectors on an n^3 grid (L = 28 n / 96 bohr), at the reduced precision system's
+    density of 8 atoms per (28 bohr)^3 (two occupied orbitals per atom)."""
+    L = n * 28.0 / 96.0
+    natom = max(2, int(round(8 * (n / 96.0) ** 3)))
+    return SystemSpec(f"learned{n}_{seed}", L, (n, n, n), 25.0, natom, 2 * natom, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, seed)
 
 
 def spec(name: str) -> SystemSpec:
