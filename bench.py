@@ -66,6 +66,13 @@ WORKLOADS = {
         "512 perturbations per GPU applied in 8 chunks of 64; one step = one chunk: PDEP 64 eigenpairs, one Davidson "
         "iteration (16384 solves)",
         "precision_reduced", 8),
+    # small case of the precision workload for profiler captures: the same 96^3 grid and 23,149-wave
+    # layout (so the same kernels and per-unit work) with 8 atoms and 16 orbitals
+    "precision_small": Workload(
+        "precision_reduced", 32, 32, 16,
+        "precision_small: L=28 bohr, 96^3 grid, |G|^2<=25, 23149 stored PWs, 8 atoms (32 KB projectors), 16 occupied, "
+        "32 perturbations per step, PDEP 16 eigenpairs, one Davidson iteration per step (512 solves)",
+        "precision_reduced", 8),
     "medium": Workload(
         "medium", 128, 128, 64,
         "medium: L=20 bohr, 64^3 grid, |G|^2<=25, 8440 stored PWs, 32 atoms (128 KB projectors), 64 occupied, "
@@ -92,6 +99,7 @@ ALU_PEAK_SOURCE = {"mixed_df": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (d
 PLANE_DRAM_BYTES_PER_UNIT = {
     (64, 1): (210.873088e6 + 167.385088e6) / 32768,  # k_plane_reg<64>: 32,768 units
     (64, 5): (210.877440e6 + 149.595648e6) / 32768,  # k_plane_pipe<15>: 32,768 units
+    (96, 7): (311.997440e6 + 249.979648e6) / 24576,  # k_plane_pipe2<96, 22>: 24,576 units
 }
 
 
@@ -526,7 +534,7 @@ def run_secondary_medium(args, stream, dev, flush):
 
 def run_learned(args):
     """The learned-preconditioner protocol: a model trained on converged solves of 32 seeded
-    systems of the family (96^3 and 128^3 grids alternating, L = 28 n / 96 bohr, |G|^2 <= 25, the
+    systems of the family (96^3 and 108^3 grids alternating, L = 28 n / 96 bohr, |G|^2 <= 25, the
     reduced precision system's atom density) is applied to 8 held-out seeds; each held-out system
     applies chi0bar to a block of perturbations to 1e-8 with TPA and with the learned scale.
     Reports CG iterations per solve, wall time (CUDA events, one warm-up apply each) and the TPA
@@ -538,7 +546,7 @@ def run_learned(args):
 
     torch.cuda.set_device(0)
     wbuild.build()
-    grids = (96, 128)
+    grids = (96, 108)  # 128^3 planes exceed the shared-memory tile of the FP64 plane kernel
     t0 = time.perf_counter()
     train = [wdf.Context(synth.make_system(synth.learned_family(k, grids[k % 2])), precision=args.precision, cg_tol=1e-8)
              for k in range(args.learned_train)]
@@ -579,7 +587,7 @@ def run_learned(args):
         "ms_per_step": tot["learned"][1], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed": "f32+f64", "mixed_df": "f32+df64+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": f"learned: train seeds 0..{args.learned_train - 1}, held-out seeds {args.learned_train}.."
-                               f"{args.learned_train + args.learned_test - 1}, grids 96^3/128^3 alternating, "
+                               f"{args.learned_train + args.learned_test - 1}, grids 96^3/108^3 alternating, "
                                f"{args.learned_npert} perturbations per held-out system, cg_tol 1e-8",
                    "precision": args.precision},
         "tpa": {"value": tot["tpa"][0] / (tot["tpa"][1] * 1e-3), "unit": UNIT, "ms": tot["tpa"][1],
@@ -671,9 +679,13 @@ def main():
                     help="learned: train the MLP preconditioner on other seeds of the family first (not timed)")
     ap.add_argument("--no-learned", dest="with_learned", action="store_false",
                     help="skip the extra timing of the learned preconditioner after the TPA headline")
-    ap.add_argument("--workload", choices=["precision", "medium", "batching", "learned"], default="precision",
-                    help="precision (the headline: 96^3, 256 orbitals, 512 perturbations in chunks of 64); medium "
+    ap.add_argument("--workload", choices=["precision", "precision_small", "medium", "batching", "learned"], default="precision",
+                    help="precision (the headline: 96^3, 256 orbitals, 512 perturbations in chunks of 64); precision_small "
+                         "(its 96^3 layout with 16 orbitals, for small-case profiler captures); medium "
                          "(64^3, 64 orbitals, 128 perturbations); batching: the uneven multi-system workload (its own line)")
+    ap.add_argument("--npert", type=int, default=0,
+                    help="perturbations per step (default: the workload's chunk, 64 for precision, 128 for medium); "
+                         "the block keeps its number of chunks")
     ap.add_argument("--fp64-npert", type=int, default=2,
                     help="perturbations of the block timed in the plain FP64 GPU form (0: skip)")
     ap.add_argument("--no-secondary", dest="secondary", action="store_false",
@@ -687,6 +699,11 @@ def main():
     ap.add_argument("--train-npert", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=600)
     args = ap.parse_args()
+    if args.npert > 0:
+        for k, wl in list(WORKLOADS.items()):
+            nch = wl.nblock // wl.chunk
+            WORKLOADS[k] = dataclasses.replace(wl, chunk=args.npert, nblock=args.npert * nch, neig=min(wl.neig, args.npert),
+                                               desc=wl.desc + f" [--npert {args.npert}: {args.npert} perturbations per step]")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batching":

@@ -219,6 +219,27 @@ int wdf_pdep_davidson(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, doubl
 int wdf_pdep_davidson_seeded(wdf_ctx *ctx, int neig, int nbasis_max, int maxiter, double tol, uint64_t seed,
                              double *lambda, double *phibar, int mem, wdf_stats *st);
 
+/* A caller's operator for wdf_davidson: out = A in for nvec half-sphere vectors, in and out
+ * [nvec][npw_h] complex in DEVICE memory of the context's GPU, owned by the library and valid
+ * for the duration of the call (out arrives zeroed). The callback runs on the thread that called
+ * wdf_davidson, after the library's stream has finished writing in; its results must be in out
+ * when it returns (synchronise whatever stream it used). Return 0, or non-zero to abort the
+ * eigensolve (wdf_davidson then returns WDF_EINVAL). */
+typedef int (*wdf_operator_fn)(void *user, int nvec, const double *in, double *out);
+
+/* The library's block Davidson on a caller's operator (Sec. 3.3: one Davidson solver serves PDEP
+ * and the BSE and TDDFT eigenproblems): the neig algebraically lowest eigenpairs of A, a
+ * Hermitian operator on the context's plane-wave basis that maps real functions to real
+ * functions (symmetric in the Gamma inner product). Same algorithm, restart rule and convergence
+ * test as wdf_pdep_davidson (||A x_a - lambda_a x_a|| <= tol), with apply(user, ...) in place of
+ * chi0bar. zero_g0: 1 keeps the G = 0 component out of the space (as for chi0bar), 0 keeps it.
+ * guess: [nguess][npw_h] start block (nguess >= neig), host or device per mem; lambda: [neig]
+ * ascending (host); vec: [neig][npw_h] orthonormal eigenvectors, host or device per mem.
+ * st: napply, davidson_iters, converged and ms are filled. Errors: WDF_EINVAL (arguments, or the
+ * callback failed), WDF_ENOCONV (best Ritz pairs returned), others as wdf_pdep_davidson. */
+int wdf_davidson(wdf_ctx *ctx, wdf_operator_fn apply, void *user, int neig, int nbasis_max, int maxiter, double tol,
+                 int zero_g0, int nguess, const double *guess, double *lambda, double *vec, int mem, wdf_stats *st);
+
 /* Bytes of the device array behind wdf_apply_hamiltonian_noalloc: 64 MiB, present on every GPU
  * that loads the library for the life of the process. */
 #define WDF_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)

@@ -338,6 +338,31 @@ struct Chi0Op : DavOp {
   }
 };
 
+// The caller's operator (wdf_davidson): internal vectors go out in the half-sphere layout to the
+// callback and its results come back into the internal layout.
+struct UserOp : DavOp {
+  wdf_ctx *c;
+  wdf_operator_fn fn;
+  void *user;
+  long long calls = 0;
+  UserOp(wdf_ctx *cc, wdf_operator_fn f, void *u) : c(cc), fn(f), user(u) {}
+  void apply(const cplx<double> *X, cplx<double> *Y, int n) override {
+    const size_t nd = 2 * (size_t)n * c->npw_h;
+    c->uop_in.ensure(nd * sizeof(double));
+    c->uop_out.ensure(nd * sizeof(double));
+    launch_int_to_ext(X, n, c->geo.ld, c->npw_h, c->t_emap.as<int>(), c->t_econj.as<int>(), c->uop_in.as<double>(), c->st);
+    WDF_CUDA_TRY(cudaMemsetAsync(c->uop_out.p, 0, nd * sizeof(double), c->st));
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));  // the callback may work on any stream
+    const int rc = fn(user, n, c->uop_in.as<double>(), c->uop_out.as<double>());
+    if (rc != 0) throw ApiFailure(WDF_EINVAL, "the operator callback returned " + std::to_string(rc));
+    ++calls;
+    const size_t bytes = sizeof(cplx<double>) * (size_t)n * c->geo.ld;
+    WDF_CUDA_TRY(cudaMemsetAsync(Y, 0, bytes, c->st));
+    launch_ext_to_int(c->uop_out.as<double>(), n, c->npw_h, c->t_emap.as<int>(), c->t_emap2.as<int>(), c->t_econj.as<int>(), nullptr, Y,
+                      c->geo.ld, c->st);
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -423,7 +448,8 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->xpdf,      &c->dvgriddf,  &c->accgriddf, &c->cb2df,  &c->drdf,    &c->oudf, &c->chol,
                   &c->ml64,      &c->ml32,      &c->mlw64,   &c->krow,     &c->rr_ref,  &c->it_ref,  &c->nfb,
                   &c->mlsums,    &c->mlwraw,    &c->tcU,     &c->tcUt,     &c->tcC,     &c->tcerr,
-                  &c->wp_phi,    &c->wp_x,      &c->wp_y,    &c->wp_vx,    &c->wp_S,    &c->wp_coef};
+                  &c->wp_phi,    &c->wp_x,      &c->wp_y,    &c->wp_vx,    &c->wp_S,    &c->wp_coef,
+                  &c->uop_in,    &c->uop_out};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {
@@ -613,6 +639,35 @@ int wdf_pdep_davidson(wdf_ctx *c, int neig, int nbasis_max, int maxiter, double 
     WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
     op.agg.converged = op.agg.converged && r.converged;
     fill_stats(st, op.agg, op.nsolve, r.napply, tm.ms());
+    if (st) st->davidson_iters = r.iters;
+    return r.converged ? WDF_OK : WDF_ENOCONV;
+  });
+}
+
+int wdf_davidson(wdf_ctx *c, wdf_operator_fn apply, void *user, int neig, int nbasis_max, int maxiter, double tol, int zero_g0,
+                 int nguess, const double *guess, double *lambda, double *vec, int mem, wdf_stats *st) {
+  if (!c) return WDF_EINVAL;
+  return guarded(c, [&] {
+    Timer tm;
+    check_mem(mem);
+    if (!apply || neig < 1 || nguess < neig || !guess || !lambda || !vec || maxiter < 1 || !(tol > 0) || nbasis_max < 0)
+      throw ApiFailure(WDF_EINVAL, "bad Davidson arguments");
+    const int dim = 2 * c->geo.nint - c->geo.len0 - (zero_g0 ? 1 : 0);
+    if (neig > dim) throw ApiFailure(WDF_EINVAL, "neig exceeds the basis dimension");
+    const int nbmax = nbasis_max > 0 ? nbasis_max : 4 * neig;
+    cplx<double> *G0 = read_in(c, c->ext_in, c->guess, guess, nguess, mem);
+    if (zero_g0) {
+      const int e0 = c->lay.col_off[0] - c->lay.col_zlo[0];
+      WDF_CUDA_TRY(cudaMemset2DAsync(G0 + e0, sizeof(cplx<double>) * c->geo.ld, 0, sizeof(cplx<double>), nguess, c->st));
+    }
+    UserOp op(c, apply, user);
+    DavResult r = davidson(c, op, G0, nguess, neig, neig, nbmax, maxiter, tol, zero_g0 != 0);
+    for (int a = 0; a < neig; ++a) lambda[a] = r.lam[a];
+    write_out(c, c->ext_out, c->dv_X.as<cplx<double>>(), neig, vec, mem);
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    SolveStats none;
+    none.converged = r.converged;
+    fill_stats(st, none, 0, r.napply, tm.ms());
     if (st) st->davidson_iters = r.iters;
     return r.converged ? WDF_OK : WDF_ENOCONV;
   });

@@ -99,6 +99,7 @@ struct wdf_ctx {
   // training-sample collection (wdf_model_add_solves): sums [3][nocc][ld] over converged solves
   wdf::DBuf mlsums, mlwraw;
   wdf::DBuf wp_phi, wp_x, wp_y, wp_vx, wp_S, wp_coef;  // wdf_apply_wp
+  wdf::DBuf uop_in, uop_out;                           // wdf_davidson: the caller's operator's in / out
   bool collect = false;
   wdf::DBuf rb, rx, rr, rAx, rwork;        // refinement: b, x, r, A x (FP64), FP32 staging
   wdf::DBuf shift, vidx_dev, thr;          // per-solve shift, orbital index, thresholds

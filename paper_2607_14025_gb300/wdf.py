@@ -113,6 +113,18 @@ class TrainStats(ctypes.Structure):
 _lib = None
 
 
+# out = A in for wdf_davidson: (user, nvec, in, out) -> status
+OPERATOR_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr: int, shape, device: int):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, False), "version": 2}
+        self.device = device
+
+
 def load(path: str = LIB_PATH):
     """Load libwdf.so (once). Raises if it is missing: the library has no fallback."""
     global _lib
@@ -134,6 +146,7 @@ def load(path: str = LIB_PATH):
         "wdf_apply_hamiltonian_noalloc": (I, [P, I, P, P]),
         "wdf_apply_chi0_multi": (I, [I, P, P, P, P, I, P]),
         "wdf_apply_wp": (I, [P, I, P, P, I, P, P, I]),
+        "wdf_davidson": (I, [P, OPERATOR_FN, P, I, I, I, D, I, I, P, P, P, I, P]),
         "wdf_half_sphere": (I, [P, D, P, P]),
         "wdf_get_gvectors": (I, [P, P]),
         "wdf_reset_error": (I, [P]),
@@ -436,6 +449,43 @@ class Context:
         out, op = self._out_like(x, x.shape[0])
         self._check(self._lib.wdf_apply_wp(self._ctx, lam.shape[0], lam.ctypes.data, pp, x.shape[0], xp, op, mem))
         return out
+
+    def davidson(self, apply, neig: int, guess, nbasis_max: int = 0, maxiter: int = 100, tol: float = 1e-10,
+                 zero_g0: bool = True):
+        """Lowest neig eigenpairs of a caller's operator by the library's Davidson (wdf_davidson).
+
+        ``apply(x, out)`` gets two complex128 CUDA tensors of shape (nvec, npw_h) that view the
+        library's buffers and must write A x into ``out`` (synchronised) before returning.
+        Returns (lambda[neig], vectors[neig, npw_h], Stats).
+        """
+        import torch
+
+        npw = self.npw_h
+        dev = self.device
+
+        def trampoline(user, nvec, pin, pout):
+            try:
+                x = torch.view_as_complex(torch.as_tensor(_DeviceArray(pin, (nvec, npw, 2), dev), device=f"cuda:{dev}"))
+                out = torch.view_as_complex(torch.as_tensor(_DeviceArray(pout, (nvec, npw, 2), dev), device=f"cuda:{dev}"))
+                apply(x, out)
+                torch.cuda.synchronize(dev)
+                return 0
+            except Exception:  # noqa: BLE001 - reported to the library as a failed callback
+                import traceback
+
+                traceback.print_exc()
+                return 1
+
+        fn = OPERATOR_FN(trampoline)
+        keep: list = []
+        p, mem = _ptr_in(guess, np.complex128, keep)
+        lam = np.empty(neig)
+        vec, vp = self._out_like(guess, neig)
+        st = Stats()
+        rc = self._lib.wdf_davidson(self._ctx, fn, None, neig, nbasis_max, maxiter, tol, 1 if zero_g0 else 0, guess.shape[0], p,
+                                    lam.ctypes.data, vp, mem, ctypes.byref(st))
+        self._check(rc, (lam, vec, st))
+        return lam, vec, st
 
     def gvectors(self) -> np.ndarray:
         """The context's Miller triples (npw_h, 3)."""

@@ -173,8 +173,9 @@ def grid_probe(n: int, seed: int = 7) -> SystemSpec:
 
 def learned_family(seed: int, n: int = 96) -> SystemSpec:
     """A member of the learned-preconditioner family: the precision system's spacing, cutoff,
-    wells and projectors on an n^3 grid (L = 28 n / 96 bohr), at the reduced precision system's
-    density of 8 atoms per (28 bohr)^3 (two occupied orbitals per atom)."""
+    wells and projectors on an n^3 grid (L = 28 n / 96 bohr; the benchmark uses n = 96 and 108),
+    at the reduced precision system's density of 8 atoms per (28 bohr)^3 (two occupied orbitals
+    per atom)."""
     L = n * 28.0 / 96.0
     natom = max(2, int(round(8 * (n / 96.0) ** 3)))
     return SystemSpec(f"learned{n}_{seed}", L, (n, n, n), 25.0, natom, 2 * natom, 12.0, 1.0, 0.8, -2.0, 5.0, 4.5, seed)

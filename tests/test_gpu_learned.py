@@ -213,3 +213,26 @@ def test_model_on_fp64_context_and_back_to_tpa():
         out2, _, st2 = c.apply_chi0(phi)
     assert np.abs(out1 - out0).max() <= 1e-9 * np.abs(out0).max()
     assert np.array_equal(out2, out0) and st2.cg_iters == st0.cg_iters  # TPA path is deterministic
+
+
+def test_learned_family_96_held_out_gain():
+    # the learned form's own family (96^3 grid, 23,149 stored plane waves, the precision system's
+    # cell and cutoff at a reduced atom count): train on 6 seeds, test on 2 held-out seeds
+    train = [wdf.Context(synth.make_system(synth.learned_family(k, 96)), precision="mixed_df", cg_tol=1e-8) for k in range(6)]
+    model, ts = wdf.train_preconditioner(train, npert=8, steps=800, lr=3e-3, seed=11)
+    for c in train:
+        c.close()
+    assert ts.loss_last < 0.5 * ts.loss_first
+    it_tpa, it_ml = 0.0, 0.0
+    for k in (32, 33):
+        s = synth.make_system(synth.learned_family(k, 96))
+        phi = synth.make_perturbations(s, 8, 700 + k)
+        with wdf.Context(s, precision="mixed_df", cg_tol=1e-10) as c:
+            out0, _, st0 = c.apply_chi0(phi)
+            c.set_model(model)
+            out1, _, st1 = c.apply_chi0(phi)
+        assert st1.converged == 1 and st1.max_residual <= 1e-10
+        assert np.abs(out1 - out0).max() <= 1e-8 * np.abs(out0).max()
+        it_tpa += st0.cg_iters / st0.nsolve
+        it_ml += st1.cg_iters / st1.nsolve
+    assert it_ml < 0.95 * it_tpa
