@@ -169,12 +169,16 @@ template <> struct Stage<double> {
   static DBuf &dv(wdf_ctx *c) { return c->dvgrid; }
   static DBuf &acc(wdf_ctx *c) { return c->accgrid; }
   static DBuf &cb2(wdf_ctx *c) { return c->cb2; }
+  static DBuf &fields(wdf_ctx *c) { return c->orbfields; }
+  static DBuf &ones(wdf_ctx *c) { return c->ones64; }
 };
 template <> struct Stage<df64> {
   static const df64 *psir(wdf_ctx *c) { return c->psirdf.as<df64>(); }
   static DBuf &dv(wdf_ctx *c) { return c->dvgriddf; }
   static DBuf &acc(wdf_ctx *c) { return c->accgriddf; }
   static DBuf &cb2(wdf_ctx *c) { return c->cb2df; }
+  static DBuf &fields(wdf_ctx *c) { return c->orbfields; }
+  static DBuf &ones(wdf_ctx *c) { return c->onesdf; }
 };
 
 // FP64 complex vectors <-> double-float complex vectors (n rows of ld)
@@ -742,13 +746,38 @@ static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, cplx<do
     cb2.ensure(sizeof(cplx<R>) * (size_t)(pp1 - pp0) * cbpair);
     accb.ensure(sizeof(cplx<R>) * (size_t)(pp1 - pp0) * ngrid);
     launch_zpass_g2r<R>(f, xR, ns, cb, st);
-    PlaneArgs<R> pa;
-    pa.cb = cb;
-    pa.cb2 = cb2.as<cplx<R>>();
-    pa.field = Stage<R>::psir(c);
-    pa.grid = accb.as<cplx<R>>();
-    pa.nocc = nocc;
-    launch_plane<R>(f, OP_ACCUM, pp1 - pp0, pa, st);
+    if (plane_accum_by_g2r<R>(f)) {
+      // per perturbation pair: every orbital's pair to real space (compile-time plane kernel), then
+      // the sum over orbitals on the grid; then the summed grids back to their column buffers
+      // (the product kernel with psi = 1)
+      DBuf &fields = Stage<R>::fields(c), &ones = Stage<R>::ones(c);
+      fields.ensure(sizeof(cplx<R>) * (size_t)nocc * ngrid);
+      if (ones.cap < sizeof(R) * ngrid) {
+        ones.ensure(sizeof(R) * ngrid);
+        launch_fill<R>(ones.as<R>(), ngrid, 1.0, st);
+      }
+      for (int pp = pp0; pp < pp1; ++pp) {
+        PlaneArgs<R> pg;
+        pg.cb = cb + (size_t)(pp - pp0) * nocc * cbpair;
+        pg.grid = fields.as<cplx<R>>();
+        launch_plane<R>(f, OP_G2R, nocc, pg, st);
+        launch_orbital_sum<R>(fields.as<cplx<R>>(), Stage<R>::psir(c), nocc, ngrid, accb.as<cplx<R>>() + (size_t)(pp - pp0) * ngrid, st);
+      }
+      PlaneArgs<R> pb;
+      pb.cb = cb2.as<cplx<R>>();
+      pb.field = ones.as<R>();
+      pb.grid = accb.as<cplx<R>>();
+      pb.nocc = 1;
+      launch_plane<R>(f, OP_PROD_R2G, pp1 - pp0, pb, st);
+    } else {
+      PlaneArgs<R> pa;
+      pa.cb = cb;
+      pa.cb2 = cb2.as<cplx<R>>();
+      pa.field = Stage<R>::psir(c);
+      pa.grid = accb.as<cplx<R>>();
+      pa.nocc = nocc;
+      launch_plane<R>(f, OP_ACCUM, pp1 - pp0, pa, st);
+    }
     EpiArgs<R> ea;
     ea.Y = drR + (size_t)(2 * pp0) * g.ld;
     ea.Y2 = ouR + (size_t)(2 * pp0) * g.ld;

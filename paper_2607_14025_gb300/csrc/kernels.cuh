@@ -51,6 +51,13 @@ template <typename T> bool launch_plane_fast(const FftCtx<T> &f, int op, int nbl
 // 5 persistent with bulk copies, 6 double-float one task per thread) exists
 template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v);
 constexpr int kPlaneVariants = 7;  // variants are numbered 1 .. kPlaneVariants
+// whether the orbital sum of the density response runs as G2R transforms + k_orbital_sum
+template <typename T> bool plane_accum_by_g2r(const FftCtx<T> &f);
+// acc[i] = sum_v psir[v][i] fields[v][i] over the ngrid points, orbitals in order
+template <typename R>
+void launch_orbital_sum(const cplx<R> *fields, const R *psir, int nocc, size_t ngrid, cplx<R> *acc, cudaStream_t st);
+// x[i] = value
+template <typename R> void launch_fill(R *x, size_t count, double value, cudaStream_t st);
 // persistent FP32 V_loc plane kernel (plane_pipe.cu); false when the geometry has no instance
 bool plane_pipe_available(const Geo &g, const int *err);
 void set_plane_pipe_limits(const Geo &g);

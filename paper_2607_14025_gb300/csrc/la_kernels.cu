@@ -723,6 +723,38 @@ template <typename Tin, typename Tout>
 __global__ void k_convert(Tout *__restrict__ y, const Tin *__restrict__ x, size_t count) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) y[t] = (Tout)x[t];
 }
+// the orbital sum of the density response on the grid: acc = sum_v psi_v(r) G2R(dpsi_v pair)(r),
+// the orbitals in ascending order (the same order as the in-plane sums)
+template <typename R>
+__global__ void k_orbital_sum(const cplx<R> *__restrict__ fields, const R *__restrict__ psir, int nocc, size_t ngrid,
+                              cplx<R> *__restrict__ acc) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ngrid; i += (size_t)gridDim.x * blockDim.x) {
+    cplx<R> a = cscal<R>(fields[i], psir[i]);
+    for (int v = 1; v < nocc; ++v) a = cadd<R>(a, cscal<R>(fields[(size_t)v * ngrid + i], psir[(size_t)v * ngrid + i]));
+    acc[i] = a;
+  }
+}
+
+template <typename R>
+void launch_orbital_sum(const cplx<R> *fields, const R *psir, int nocc, size_t ngrid, cplx<R> *acc, cudaStream_t st) {
+  if (nocc <= 0) return;
+  launch("orbital_sum", bits_of<R>(), k_orbital_sum<R>, dim3((int)std::min<size_t>(8192, (ngrid + 255) / 256)), dim3(256), 0, st, fields,
+         psir, nocc, ngrid, acc);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+template void launch_orbital_sum<double>(const cplx<double> *, const double *, int, size_t, cplx<double> *, cudaStream_t);
+template void launch_orbital_sum<df64>(const cplx<df64> *, const df64 *, int, size_t, cplx<df64> *, cudaStream_t);
+
+template <typename R> __global__ void k_fill(R *__restrict__ x, size_t count, R value) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) x[i] = value;
+}
+template <typename R> void launch_fill(R *x, size_t count, double value, cudaStream_t st) {
+  launch("fill", bits_of<R>(), k_fill<R>, dim3((int)std::min<size_t>(8192, (count + 255) / 256)), dim3(256), 0, st, x, count, R(value));
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+template void launch_fill<double>(double *, size_t, double, cudaStream_t);
+template void launch_fill<df64>(df64 *, size_t, double, cudaStream_t);
+
 template <typename Tin, typename Tout> void launch_convert(const Geo &, Tout *y, const Tin *x, size_t count, cudaStream_t st) {
   if (count == 0) return;
   launch("convert", bits_of<Tout>(), k_convert<Tin, Tout>, dim3((int)std::min<size_t>(8192, (count + 255) / 256)), dim3(256), 0, st, y, x, count);

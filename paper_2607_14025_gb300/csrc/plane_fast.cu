@@ -400,6 +400,23 @@ template <typename T> bool plane_variant_available(const FftCtx<T> &f, int v) {
   }
   return false;
 }
+// the orbital sum of the density response as compile-time G2R transforms of each orbital's pair
+// followed by a separate sum over orbitals (k_orbital_sum): FP64-class arithmetic on grids with a
+// compile-time Stockham kernel, except the 64 x 64 double-float planes, whose kernel sums in place
+template <typename T> bool plane_accum_by_g2r(const FftCtx<T> &f) {
+  if constexpr (std::is_same<T, float>::value) {
+    return false;
+  } else {
+    if (f.jidx == nullptr || f.vloc_variant == 3) return false;
+    if constexpr (std::is_same<T, df64>::value)
+      if (plane_df_available(f.g, f.jidx)) return false;
+    return plane_fast_supported(f.g.n1, f.g.n2) || (!std::is_same<T, double>::value && plane_more_supported(f.g.n1, f.g.n2));
+  }
+}
+template bool plane_accum_by_g2r<double>(const FftCtx<double> &);
+template bool plane_accum_by_g2r<float>(const FftCtx<float> &);
+template bool plane_accum_by_g2r<df64>(const FftCtx<df64> &);
+
 template bool plane_variant_available<double>(const FftCtx<double> &, int);
 template bool plane_variant_available<float>(const FftCtx<float> &, int);
 template bool plane_variant_available<df64>(const FftCtx<df64> &, int);

@@ -29,6 +29,27 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
   return d;
 }
 
+// 64-byte-swizzled K-major rows (16 FP32 values): 16-byte chunk c (0..3) of row r sits at chunk
+// position c XOR ((r / 2) mod 4) inside its 8-row, 512-byte atom
+__host__ __device__ __forceinline__ int swz64_off(int r, int c) { return (r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r >> 1) & 3)) << 4); }
+
+// shared-memory matrix descriptor: K-major, SWIZZLE_64B, stride 512 B between 8-row atoms
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;           // descriptor version of the sm_100 family
+  d |= (uint64_t)4 << 61;           // 64-byte swizzle
+  return d;
+}
+
+// 16-byte asynchronous global -> shared copy (cp.async, L2 only); bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);

@@ -4,12 +4,17 @@
 // Complex vectors are read as real rows of 2 N_int values, so both are real GEMMs with K-major
 // operands. FP32 accuracy from TF32 units by the three-term split a b ~ a_h b_h + a_h b_l + a_l b_h
 // with a_h the upper 19 bits of a and a_l = a - a_h (the dropped a_l b_l is ~2^-22 |a b|).
-// Operand tiles are staged through registers (the low parts and the zero padding are made on
-// the way) into 128-byte-swizzled shared memory, two stages deep; one thread issues the MMAs and
-// commits them to the stage's mbarrier; accumulators sit in TMEM and the epilogue reads them with
-// tcgen05.ld. Every mbarrier wait is bounded: on expiry the kernel raises a flag, waits (bounded)
-// for what it issued, frees its TMEM and returns.
+// Operand tiles arrive in 64-byte-swizzled shared memory by tensor-memory-access copies (tensor
+// maps made per launch; reads past a matrix's end give zeros), four stages deep, in
+// warp-specialised pipelines coupled by mbarriers: one thread loads, one thread issues the MMAs
+// and commits them to the stage's mbarrier; accumulators sit in TMEM and the epilogues read them
+// with tcgen05.ld. Every mbarrier wait is bounded: on expiry the kernel raises a flag, waits
+// (bounded) for what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdlib>
+#include <mutex>
 
 #include "engine.cuh"
 #include "tc.cuh"
@@ -19,64 +24,84 @@ namespace wdf {
 namespace {
 
 constexpr int TM = 128;              // MMA M: solves per tile
-constexpr int TK = 32;               // K values per stage (one 128-byte row)
-constexpr int XB = TM * 128;         // bytes of a 128-row operand tile
 constexpr long kWaitLimit = 1L << 26;  // polls of an mbarrier before giving up
-// chunks per FP32 accumulation chain of the Gram: longer chains lose accuracy (the sums run over
-// 2 N_int products), so every kPromote chunks the partial sums move into the FP64 output
-constexpr int kPromote = 32;
+// chunks (of 16 K values) per FP32 accumulation chain of the Gram: longer chains lose accuracy
+// (the sums run over 2 N_int products), so every kPromote chunks (2,048 K values) the partial sums
+// move into the FP64 output
+constexpr int kPromote = 128;
 
 __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
   return (unsigned char *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
 }
 
-// stage a 16-byte piece (hi and lo) into swizzled tiles
-__device__ __forceinline__ void put(unsigned char *hi, unsigned char *lo, int row, int q, float4 v) {
-  const int o = tc::swz_off(row, q);
-  *reinterpret_cast<float4 *>(hi + o) = v;
-  *reinterpret_cast<float4 *>(lo + o) = make_float4(tc::tf32_low(v.x), tc::tf32_low(v.y), tc::tf32_low(v.z), tc::tf32_low(v.w));
-}
+// S (+ split partials) = U_w X^T; grid (solve tiles, splits, chunks of U rows). Warp-specialised
+// pipeline over kGramStages shared-memory stages of kGramK values (64-byte swizzled K-major rows):
+//   warp 0   one thread loads the X, U hi and U lo tiles of a stage with tensor-memory-access
+//            copies (cp.async.bulk.tensor, completion counted in bytes on the stage's full barrier);
+//   warp 1   one thread issues the stage's 3 x 2 MMAs (hi hi, hi lo, lo hi) and commits them to the
+//            stage's empty barrier (the loader's go-ahead to refill it);
+//   warps 4-7 make the low parts of X in shared memory once a stage has landed (lo barrier);
+//   warps 8-11 move each finished FP32 accumulation chain (kPromote stages) from its TMEM half into
+//            the FP64 output (the first chain stores, later ones add) while the MMAs fill the
+//            other half, then release the half (tfree barrier).
+// No thread waits on another through a block-wide barrier inside the loop; every mbarrier wait is
+// bounded and a role that gives up makes the others give up at their next wait.
+constexpr int kGramK = 16;                 // K values per stage (one 64-byte row)
+constexpr int kGramStages = 4;
+constexpr int kGramXB = TM * kGramK * 4;   // bytes of the 128-row X stage
+constexpr int kGramThreads = 384;
 
-// element f .. f+3 of a row, zero at and beyond kf
-__device__ __forceinline__ float4 load_masked(const float *row, int f, int kf) {
-  if (f + 3 < kf) return *reinterpret_cast<const float4 *>(row + f);
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (f < kf) v.x = row[f];
-  if (f + 1 < kf) v.y = row[f + 1];
-  if (f + 2 < kf) v.z = row[f + 2];
-  return v;
-}
-
-// S (+ split partials) = U_w X^T; grid (solve tiles, splits), 256 threads. The operands of chunk
-// i + 1 are loaded into registers while the MMAs of chunk i run, so global latency overlaps them.
-constexpr int UPT = 8;  // U pieces per thread and operand part at most (256 rows x 8 pieces / 256 threads)
-
-// blockIdx.z picks a chunk of at most kGramRows rows of U (rows z kGramRows ...): a CTA holds the
-// accumulators of 128 solves x one chunk in TMEM, so U of any height runs in chunks.
+// blockIdx.z picks a chunk of rows of U (rows z nbox ...; nbox <= kGramRows, the chunks as even as
+// multiples of 32 allow): a CTA holds the accumulators of 128 solves x one chunk in TMEM, so U of
+// any height runs in chunks.
 constexpr int kGramRows = 256;
 
-__global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restrict__ X, int nb, const float *__restrict__ Uhi,
-                                                    const float *__restrict__ Ulo, int na_all, double *__restrict__ out, int ldo,
-                                                    int ch_per_split, size_t split_stride, int *__restrict__ err) {
+__host__ __device__ constexpr int gram_stage_bytes(int nbox) { return 2 * kGramXB + 2 * nbox * kGramK * 4; }
+
+__device__ __forceinline__ void tma_load2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(map), "r"(x), "r"(y), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// nbox: rows of the U boxes the tensor maps load (the stage layout); na_all: rows of U
+__global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mUh,
+                                                             const __grid_constant__ CUtensorMap mUl, Geo g, int nb, int na_all, int nbox,
+                                                             double *__restrict__ out, int ldo, int ch_per_split, size_t split_stride,
+                                                             int *__restrict__ err) {
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = align1024(smraw);
-  const int j0 = blockIdx.z * kGramRows;
-  const int na = min(kGramRows, na_all - j0), nu = ((na + 31) / 32) * 32;
-  Uhi += (size_t)j0 * 2 * g.ld;
-  Ulo += (size_t)j0 * 2 * g.ld;
+  const int j0 = blockIdx.z * nbox;
+  const int na = min(nbox, na_all - j0), nu = ((na + 31) / 32) * 32;
   out += (size_t)j0 * ldo;
-  const int UB = nu * 128, SB = 2 * XB + 2 * UB;  // the launch sizes shared memory for the largest chunk
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * SB);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + 2 * SB + 16);
+  const int UB = nbox * kGramK * 4, SB = gram_stage_bytes(nbox);
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + kGramStages * SB);
+  uint64_t *lo = full + kGramStages, *empty = lo + kGramStages, *chain = empty + kGramStages, *tfree = chain + 2;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(tfree + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s0 = blockIdx.x * TM;
-  const int kf = 2 * g.nint, ldf = 2 * g.ld;
-  const int nch = (kf + TK - 1) / TK;
+  const int kf = 2 * g.nint;
+  const int nch = (kf + kGramK - 1) / kGramK;
   const int c0 = blockIdx.y * ch_per_split, c1 = min(nch, c0 + ch_per_split);
-  const int upt = (nu * 8) / 256;  // nu is a multiple of 32, so whole pieces per thread
+  const int n = max(0, c1 - c0);
+  const int nchains = (n + kPromote - 1) / kPromote;
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int i = 0; i < kGramStages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&lo[i], 4);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      tc::mbar_init(&chain[h], 1);
+      tc::mbar_init(&tfree[h], 4);
+    }
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(slot, 512);
@@ -84,107 +109,111 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(Geo g, const float *__restri
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-  const uint32_t idesc = tc::idesc_tf32(TM, nu);
-  // accumulation chains of kPromote chunks alternate between the two TMEM halves; a finished
-  // chain is added into the FP64 output while the next one accumulates in the other half
-  const int qd = warp & 3, hh = warp >> 2, orow = 32 * qd + lane, osol = s0 + orow;
-  double *o = out + (size_t)blockIdx.y * split_stride;
-  auto promote = [&](int p) {  // the first chain stores, later chains add
-    tc::fence_after_sync();
-    const uint32_t base = tmem + (uint32_t)((p & 1) * 256);
-    const int halfc = nu / 2;
-    for (int cg = 0; cg < halfc; cg += 16) {
-      const int col = hh * halfc + cg;
-      float v[16];
-      tc::tmem_ld16(base + ((uint32_t)(32 * qd) << 16) + (uint32_t)col, v);
-      if (osol < nb)
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (col + k < na) {
-            double *d = o + (size_t)(col + k) * ldo + osol;
-            *d = p == 0 ? (double)v[k] : *d + (double)v[k];
-          }
-    }
-    tc::fence_before_sync();
-  };
-  int promoted = 0;
-  float4 rx[4], rh[UPT], rl[UPT];
-  auto fetch = [&](int c) {
-    const int f0 = c * TK;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      rx[u] = (s0 + row < nb) ? load_masked(X + (size_t)(s0 + row) * ldf, f0 + 4 * q, kf) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < UPT; ++u) {
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      rh[u] = rl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (u < upt && row < na) {
-        rh[u] = *reinterpret_cast<const float4 *>(Uhi + (size_t)row * ldf + f0 + 4 * q);
-        rl[u] = *reinterpret_cast<const float4 *>(Ulo + (size_t)row * ldf + f0 + 4 * q);
+  bool fail = false;
+  if (warp == 0) {
+    if (lane == 0) {  // loads
+      int issued = 0;
+      for (int i = 0; i < n; ++i) {
+        const int st = i % kGramStages, k = i / kGramStages;
+        if (k > 0 && !tc::mbar_wait(&empty[st], (k - 1) & 1, kWaitLimit)) {
+          fail = true;
+          break;
+        }
+        unsigned char *S = sm + st * SB;
+        const int f0 = (c0 + i) * kGramK;
+        mbar_expect_tx(&full[st], (uint32_t)(kGramXB + 2 * UB));
+        tma_load2d(S, &mX, f0, s0, &full[st]);
+        tma_load2d(S + 2 * kGramXB, &mUh, f0, j0, &full[st]);
+        tma_load2d(S + 2 * kGramXB + UB, &mUl, f0, j0, &full[st]);
+        issued = i + 1;
       }
+      // every copy issued lands before the block's shared memory goes away
+      for (int i = max(0, issued - kGramStages); i < issued; ++i)
+        if (!tc::mbar_wait(&full[i % kGramStages], (i / kGramStages) & 1, kWaitLimit)) fail = true;
     }
-  };
-  if (c0 < c1) fetch(c0);
-  int issued = 0;
-  bool ok = true;
-  for (int c = c0; c < c1; ++c) {
-    const int i = c - c0, st = i & 1;
-    unsigned char *S = sm + st * SB;
-    if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
-    if (!ok) break;
-    if (i >= 2 && (i - 2) % kPromote == kPromote - 1) {  // chunk i - 2 closed a chain: its MMAs are done
-      promote((i - 2) / kPromote);
-      promoted = (i - 2) / kPromote + 1;
-    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMAs
+      const uint32_t idesc = tc::idesc_tf32(TM, nu);
+      int issued = 0;
+      for (int i = 0; i < n; ++i) {
+        const int st = i % kGramStages, k = i / kGramStages, p = i / kPromote, first = i % kPromote;
+        if (first == 0 && p >= 2 && !tc::mbar_wait(&tfree[p & 1], ((p - 2) >> 1) & 1, kWaitLimit)) {
+          fail = true;
+          break;
+        }
+        if (!tc::mbar_wait(&lo[st], k & 1, kWaitLimit)) {
+          fail = true;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t base = tc::smem_u32(sm + st * SB);
+        const uint32_t acc = tmem + (uint32_t)((p & 1) * 256);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int t = tid + 256 * u;
-      put(S, S + XB, t >> 3, t & 7, rx[u]);
-    }
+        for (int term = 0; term < 3; ++term) {
+          const uint32_t a = base + (term == 2 ? kGramXB : 0), b = base + 2 * kGramXB + (term == 1 ? UB : 0);
 #pragma unroll
-    for (int u = 0; u < UPT; ++u) {
-      const int t = tid + 256 * u;
-      if (u < upt) {
-        const int o = tc::swz_off(t >> 3, t & 7);
-        *reinterpret_cast<float4 *>(S + 2 * XB + o) = rh[u];
-        *reinterpret_cast<float4 *>(S + 2 * XB + UB + o) = rl[u];
+          for (int ks = 0; ks < kGramK / 8; ++ks)
+            tc::mma_tf32(acc, tc::desc_sw64(a + 32 * ks), tc::desc_sw64(b + 32 * ks), idesc, (first | term | ks) ? 1u : 0u);
+        }
+        tc::mma_commit(&empty[st]);
+        if (first == kPromote - 1 || i == n - 1) tc::mma_commit(&chain[p & 1]);
+        issued = i + 1;
       }
+      if (issued > 0 && !tc::mbar_wait(&empty[(issued - 1) % kGramStages], ((issued - 1) / kGramStages) & 1, kWaitLimit))
+        fail = true;  // the MMAs issued have finished with TMEM and shared memory
     }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
+  } else if (warp >= 4 && warp < 8) {  // low parts of X
+    const int t0 = tid - 128;
+    for (int i = 0; i < n; ++i) {
+      const int st = i % kGramStages, k = i / kGramStages;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], k & 1, kWaitLimit))) {
+        fail = true;
+        break;
+      }
+      unsigned char *S = sm + st * SB;
+#pragma unroll
+      for (int u = 0; u < kGramXB / 16 / 128; ++u) {
+        const int t = t0 + 128 * u;
+        const float4 v = *reinterpret_cast<const float4 *>(S + 16 * t);
+        *reinterpret_cast<float4 *>(S + kGramXB + 16 * t) =
+            make_float4(tc::tf32_low(v.x), tc::tf32_low(v.y), tc::tf32_low(v.z), tc::tf32_low(v.w));
+      }
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&lo[st]);
+    }
+  } else if (warp >= 8) {  // finished chains out of TMEM; warp w reads TMEM lanes 32 (w mod 4) ...
+    const int qd = warp & 3, orow = 32 * qd + lane, osol = s0 + orow;
+    double *o = out + (size_t)blockIdx.y * split_stride;
+    for (int p = 0; p < nchains; ++p) {
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&chain[p & 1], (p >> 1) & 1, kWaitLimit))) {
+        fail = true;
+        break;
+      }
       tc::fence_after_sync();
-      const uint32_t base = tc::smem_u32(S);
-      const uint32_t acc = tmem + (uint32_t)(((i / kPromote) & 1) * 256);
-      const int first = i % kPromote;
+      const uint32_t base = tmem + (uint32_t)((p & 1) * 256) + ((uint32_t)(32 * qd) << 16);
+      for (int col = 0; col < nu; col += 16) {
+        float v[16];
+        tc::tmem_ld16(base + (uint32_t)col, v);
+        if (osol < nb) {
+          double old[16];  // all loads in flight before the adds and stores
 #pragma unroll
-      for (int term = 0; term < 3; ++term) {
-        const uint32_t a = base + (term == 2 ? XB : 0), b = base + 2 * XB + (term == 1 ? UB : 0);
+          for (int kk = 0; kk < 16; ++kk) old[kk] = (p > 0 && col + kk < na) ? o[(size_t)(col + kk) * ldo + osol] : 0.0;
 #pragma unroll
-        for (int ks = 0; ks < TK / 8; ++ks)
-          tc::mma_tf32(acc, tc::desc_sw128(a + 32 * ks), tc::desc_sw128(b + 32 * ks), idesc, (first | term | ks) ? 1u : 0u);
+          for (int kk = 0; kk < 16; ++kk)
+            if (col + kk < na) o[(size_t)(col + kk) * ldo + osol] = old[kk] + (double)v[kk];
+        }
       }
-      tc::mma_commit(&bar[st]);
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[p & 1]);
     }
-    ++issued;
-    if (c + 1 < c1) fetch(c + 1);  // in flight while the MMAs run
+    if (n == 0 && osol < nb)  // an empty K range still owns its part of the output
+      for (int col = 0; col < na; ++col) o[(size_t)col * ldo + osol] = 0.0;
   }
-  // the last commit covers every MMA issued
-  bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
-  done = __syncthreads_and(done) && ok && issued == c1 - c0;
-  if (done) {
-    if (issued == 0) {  // an empty K range still owns its part of the output
-      if (osol < nb)
-        for (int col = hh * (nu / 2); col < (hh + 1) * (nu / 2) && col < na; ++col) o[(size_t)col * ldo + osol] = 0.0;
-    }
-    for (int p = promoted; p * kPromote < issued; ++p) promote(p);  // the chains still in TMEM (at most two)
-  } else if (tid == 0) {
-    atomicExch(err, 1);
-  }
-  tc::fence_before_sync();
-  __syncthreads();
+  fail = __syncthreads_or(fail);
+  if (fail && tid == 0) atomicExch(err, 1);
+  tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
@@ -221,28 +250,36 @@ __global__ void k_tc_coef(const double *__restrict__ S, int ldc, const double *_
 }
 
 // Y = c0 Y + Cd Ut^T on float rows (2 N_int), partial <P_s, Y_s> per 128-element tile;
-// grid (solve tiles, 256-value tiles), 256 threads. Operands of the next K chunk are fetched into
-// registers while the MMAs run; the finished tile goes TMEM -> shared memory, then each warp
-// updates whole rows of Y with coalesced accesses and reduces its row's partial inner product.
+// grid (solve tiles, 256-value tiles), 256 threads. The K loop (K = rows of U, in stages of
+// kGramK values, kGramStages deep) is warp-specialised: one thread of warp 0 loads the C (hi, lo)
+// and U^T (hi, lo) tiles with tensor-memory-access copies, one thread of warp 1 issues the MMAs;
+// the finished tile goes TMEM -> shared memory, then each warp updates whole rows of Y with
+// coalesced accesses and reduces its row's partial inner product.
 constexpr int DP = 260;  // shared row pitch of the result tile (floats): conflict-free float4 stores
+constexpr int kLinTN = 256;
+constexpr int kLinAB = TM * kGramK * 4, kLinBB = kLinTN * kGramK * 4, kLinSB = 2 * kLinAB + 2 * kLinBB;
 
-__global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict__ Y, int ny, const float *__restrict__ Chi,
-                                                       const float *__restrict__ Clo, int kp, const float *__restrict__ Uthi,
-                                                       const float *__restrict__ Utlo, float c0, const float *__restrict__ P,
+__global__ void __launch_bounds__(256, 1) k_lincomb_tc(const __grid_constant__ CUtensorMap mCh, const __grid_constant__ CUtensorMap mCl,
+                                                       const __grid_constant__ CUtensorMap mUh, const __grid_constant__ CUtensorMap mUl,
+                                                       Geo g, float *__restrict__ Y, int ny, int kp, float c0, const float *__restrict__ P,
                                                        double *__restrict__ part, int nchunk, int *__restrict__ err) {
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = align1024(smraw);
-  constexpr int TN = 256, BB = TN * 128, SB = 2 * XB + 2 * BB;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * SB);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + 2 * SB + 16);
+  constexpr int TN = kLinTN;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + kGramStages * kLinSB);
+  uint64_t *empty = full + kGramStages, *done_bar = empty + kGramStages;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(done_bar + 1);
   float *D = reinterpret_cast<float *>(sm);  // result tile [128][DP], over the operand stages
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s0 = blockIdx.x * TM, f0 = blockIdx.y * TN;
   const int kf = 2 * g.nint, ldf = 2 * g.ld;
-  const int nkc = kp / TK;
+  const int nkc = kp / kGramK;
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int i = 0; i < kGramStages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done_bar, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(slot, 256);
@@ -250,68 +287,54 @@ __global__ void __launch_bounds__(256, 1) k_lincomb_tc(Geo g, float *__restrict_
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-  const uint32_t idesc = tc::idesc_tf32(TM, TN);
-  float4 ah[4], al[4], bh[8], bl[8];
-  auto fetch = [&](int i) {
-    const int k0 = i * TK;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {  // coefficients: 128 solve rows x 8 pieces (hi, lo precomputed)
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      ah[u] = al[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (s0 + row < ny) {
-        ah[u] = *reinterpret_cast<const float4 *>(Chi + (size_t)(s0 + row) * kp + k0 + 4 * q);
-        al[u] = *reinterpret_cast<const float4 *>(Clo + (size_t)(s0 + row) * kp + k0 + 4 * q);
+  bool fail = false;
+  if (warp == 0 && lane == 0) {  // loads
+    int issued = 0;
+    for (int i = 0; i < nkc; ++i) {
+      const int st = i % kGramStages, k = i / kGramStages;
+      if (k > 0 && !tc::mbar_wait(&empty[st], (k - 1) & 1, kWaitLimit)) {
+        fail = true;
+        break;
       }
+      unsigned char *S = sm + st * kLinSB;
+      const int k0 = i * kGramK;
+      mbar_expect_tx(&full[st], (uint32_t)kLinSB);
+      tma_load2d(S, &mCh, k0, s0, &full[st]);
+      tma_load2d(S + kLinAB, &mCl, k0, s0, &full[st]);
+      tma_load2d(S + 2 * kLinAB, &mUh, k0, f0, &full[st]);
+      tma_load2d(S + 2 * kLinAB + kLinBB, &mUl, k0, f0, &full[st]);
+      issued = i + 1;
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {  // U transposed: 256 value rows x 8 pieces
-      const int t = tid + 256 * u, row = t >> 3, q = t & 7;
-      bh[u] = bl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (f0 + row < kf) {
-        bh[u] = *reinterpret_cast<const float4 *>(Uthi + (size_t)(f0 + row) * kp + k0 + 4 * q);
-        bl[u] = *reinterpret_cast<const float4 *>(Utlo + (size_t)(f0 + row) * kp + k0 + 4 * q);
+    for (int i = max(0, issued - kGramStages); i < issued; ++i)
+      if (!tc::mbar_wait(&full[i % kGramStages], (i / kGramStages) & 1, kWaitLimit)) fail = true;
+  } else if (warp == 1 && lane == 0) {  // MMAs: hi hi, hi lo, lo hi
+    const uint32_t idesc = tc::idesc_tf32(TM, TN);
+    int issued = 0;
+    for (int i = 0; i < nkc; ++i) {
+      const int st = i % kGramStages, k = i / kGramStages;
+      if (!tc::mbar_wait(&full[st], k & 1, kWaitLimit)) {
+        fail = true;
+        break;
       }
-    }
-  };
-  fetch(0);
-  int issued = 0;
-  bool ok = true;
-  for (int i = 0; i < nkc; ++i) {
-    const int st = i & 1;
-    unsigned char *S = sm + st * SB;
-    if (i >= 2) ok = __syncthreads_and(ok && tc::mbar_wait(&bar[st], ((i - 2) >> 1) & 1, kWaitLimit));
-    if (!ok) break;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int t = tid + 256 * u, o = tc::swz_off(t >> 3, t & 7);
-      *reinterpret_cast<float4 *>(S + o) = ah[u];
-      *reinterpret_cast<float4 *>(S + XB + o) = al[u];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = tid + 256 * u, o = tc::swz_off(t >> 3, t & 7);
-      *reinterpret_cast<float4 *>(S + 2 * XB + o) = bh[u];
-      *reinterpret_cast<float4 *>(S + 2 * XB + BB + o) = bl[u];
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t base = tc::smem_u32(S);
+      const uint32_t base = tc::smem_u32(sm + st * kLinSB);
 #pragma unroll
       for (int term = 0; term < 3; ++term) {
-        const uint32_t a = base + (term == 2 ? XB : 0), b = base + 2 * XB + (term == 1 ? BB : 0);
+        const uint32_t a = base + (term == 2 ? kLinAB : 0), b = base + 2 * kLinAB + (term == 1 ? kLinBB : 0);
 #pragma unroll
-        for (int ks = 0; ks < TK / 8; ++ks)
-          tc::mma_tf32(tmem, tc::desc_sw128(a + 32 * ks), tc::desc_sw128(b + 32 * ks), idesc, (i | term | ks) ? 1u : 0u);
+        for (int ks = 0; ks < kGramK / 8; ++ks)
+          tc::mma_tf32(tmem, tc::desc_sw64(a + 32 * ks), tc::desc_sw64(b + 32 * ks), idesc, (i | term | ks) ? 1u : 0u);
       }
-      tc::mma_commit(&bar[st]);
+      tc::mma_commit(&empty[st]);
+      issued = i + 1;
     }
-    ++issued;
-    if (i + 1 < nkc) fetch(i + 1);
+    if (issued == nkc) tc::mma_commit(done_bar);  // arrives once every MMA has completed
+    else if (issued > 0)
+      (void)tc::mbar_wait(&empty[(issued - 1) % kGramStages], ((issued - 1) / kGramStages) & 1, kWaitLimit);
   }
-  bool done = issued == 0 ? true : tc::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitLimit);
-  done = __syncthreads_and(done) && ok && issued == nkc;
+  fail = __syncthreads_or(fail);
+  bool done = !fail && (nkc == 0 || tc::mbar_wait(done_bar, 0, kWaitLimit));
+  done = __syncthreads_and(done);
   if (done) {
     // every MMA has completed, so the operand stages are free: TMEM -> D[128][DP]
     tc::fence_after_sync();
@@ -414,14 +437,33 @@ __global__ void k_tc_prep_u(Geo g, const float2 *__restrict__ U, int na, int kp,
   }
 }
 
-size_t gram_tc_smem(int nu) { return 1024 + 2 * (size_t)(2 * XB + 2 * nu * 128) + 64; }
-size_t lincomb_tc_smem() { return 1024 + 2 * (size_t)(2 * XB + 2 * 256 * 128) + 64; }
+size_t gram_tc_smem(int nbox) { return 1024 + (size_t)kGramStages * gram_stage_bytes(nbox) + 8 * (3 * kGramStages + 4) + 16; }
+size_t lincomb_tc_smem() {
+  const size_t stages = (size_t)kGramStages * kLinSB, tile = sizeof(float) * (size_t)TM * DP;
+  return 1024 + std::max(stages, tile) + 8 * (2 * kGramStages + 1) + 16;
+}
 
 }  // namespace
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
 bool tc_enabled() {
   static const bool on = std::getenv("WDF_NO_TC") == nullptr;
-  return on;
+  return on && tmap_encoder() != nullptr;
 }
 
 int tc_rows(int na) { return ((na + 31) / 32) * 32; }
@@ -438,10 +480,10 @@ void launch_tc_prep_u(const Geo &g, const float2 *U, int na, float *uwh, float *
 }
 
 // K splits of the Gram: one CTA per SM (shared memory), so the launch runs in waves of nsm CTAs;
-// choose the split count (at most nch / 8, so that each CTA keeps a pipeline of >= 8 chunks)
-// that minimises waves x (chunks per CTA + 6), the 6 standing for a CTA's partial-sum write
-// (128 x 192 doubles, about the bytes of a dozen X chunks, written without waiting), the smaller
-// count on ties (fewer partial sums to add)
+// choose the split count (at most nch / 16, so that each CTA keeps a pipeline of >= 16 chunks)
+// that minimises waves x (chunks per CTA + 12), the 12 standing for a CTA's partial-sum write
+// (128 x 192 doubles, about the bytes of two dozen 16-value X chunks, written without waiting),
+// the smaller count on ties (fewer partial sums to add)
 static int gram_tc_splits(int nch, int tiles) {
   static int nsm = 0;
   if (nsm == 0) {
@@ -449,12 +491,12 @@ static int gram_tc_splits(int nch, int tiles) {
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 152;
   }
-  const int smax = std::max(1, std::min(nch / 8, 4 * ((nsm + tiles - 1) / tiles)));
+  const int smax = std::max(1, std::min(nch / 16, 4 * ((nsm + tiles - 1) / tiles)));
   long best = -1;
   int bs = 1;
   for (int sp = 1; sp <= smax; ++sp) {
     const long waves = ((long)tiles * sp + nsm - 1) / nsm, per = (nch + sp - 1) / sp;
-    const long cost = waves * (per + 6);
+    const long cost = waves * (per + 12);
     if (best < 0 || cost < best) {
       best = cost;
       bs = sp;
@@ -464,35 +506,50 @@ static int gram_tc_splits(int nch, int tiles) {
 }
 
 size_t gram_tc_work_doubles(const Geo &g, int na, int nb) {
-  const int nch = (2 * g.nint + TK - 1) / TK;
+  const int nch = (2 * g.nint + kGramK - 1) / kGramK;
   const int tiles = ((nb + TM - 1) / TM) * ((na + kGramRows - 1) / kGramRows);
   const int nsplit = gram_tc_splits(nch, tiles);
   return nsplit > 1 ? (size_t)nsplit * na * nb : 0;
+}
+
+// rows of kf FP32 values with ldf values between row starts, read in boxes of kGramK x box_rows
+// into 64-byte swizzled shared memory; reads past the last row or value return zeros
+static CUtensorMap rows_map(const float *base, int kf, int rows, int ldf, int box_rows) {
+  CUtensorMap m;
+  const cuuint64_t dim[2] = {(cuuint64_t)kf, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)ldf * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kGramK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = tmap_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dim, stride, box, es,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw ApiFailure(WDF_EINVAL, "tensor map encoding failed (" + std::to_string((int)r) + ")");
+  return m;
 }
 
 void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, const float *uwl, int na, double *out, double *work,
                     size_t work_cap, int *err, cudaStream_t st) {
   if (nb <= 0 || na <= 0) return;
   const int nmc = (na + kGramRows - 1) / kGramRows;
-  const int nu = tc_rows(std::min(na, kGramRows));
-  const int nch = (2 * g.nint + TK - 1) / TK;
+  const int nbox = tc_rows((na + nmc - 1) / nmc);  // even chunks of U rows
+  const int kf = 2 * g.nint, ldf = 2 * g.ld;
+  const int nch = (kf + kGramK - 1) / kGramK;
   const int tiles = (nb + TM - 1) / TM;
   int nsplit = gram_tc_splits(nch, tiles * nmc);
   if ((size_t)nsplit * na * nb > work_cap) nsplit = 1;
   const int per = (nch + nsplit - 1) / nsplit;
   nsplit = (nch + per - 1) / per;
-  if (nsplit == 1) {
-    launch("gram", 32, k_gram_tc, dim3(tiles, 1, nmc), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, out, nb, per, (size_t)0,
-           err);
-  } else {
-    const size_t stride = (size_t)na * nb;
-    launch("gram", 32, k_gram_tc, dim3(tiles, nsplit, nmc), dim3(256), gram_tc_smem(nu), st, g, X, nb, uwh, uwl, na, work, nb, per,
-           stride, err);
-    WDF_CUDA_TRY(cudaGetLastError());
+  const CUtensorMap mX = rows_map(X, kf, nb, ldf, TM), mUh = rows_map(uwh, kf, na, ldf, nbox), mUl = rows_map(uwl, kf, na, ldf, nbox);
+  double *dst = nsplit == 1 ? out : work;
+  const size_t stride = nsplit == 1 ? (size_t)0 : (size_t)na * nb;
+  launch("gram", 32, k_gram_tc, dim3(tiles, nsplit, nmc), dim3(kGramThreads), gram_tc_smem(nbox), st, mX, mUh, mUl, g, nb, na, nbox, dst,
+         nb, per, stride, err);
+  WDF_CUDA_TRY(cudaGetLastError());
+  if (nsplit > 1) {
     launch("gram_sum", 0, k_tc_sum_splits, dim3((unsigned)(((size_t)na * nb + 255) / 256)), dim3(256), 0, st, (const double *)work,
            nsplit, stride, out, na, nb, nb);
+    WDF_CUDA_TRY(cudaGetLastError());
   }
-  WDF_CUDA_TRY(cudaGetLastError());
 }
 
 void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc, const double *d, int na, float *chi, float *clo,
@@ -501,9 +558,11 @@ void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc,
   const int kp = tc_rows(na);
   launch("lincomb", 32, k_tc_coef, dim3((ny + 31) / 32, (kp + 31) / 32), dim3(32, 8), 0, st, S, ldc, d, na, ny, kp, chi, clo);
   WDF_CUDA_TRY(cudaGetLastError());
-  const int ntile = (2 * g.nint + 255) / 256;
-  launch("lincomb", 32, k_lincomb_tc, dim3((ny + TM - 1) / TM, ntile), dim3(256), lincomb_tc_smem(), st, g, Y, ny, (const float *)chi,
-         (const float *)clo, kp, uth, utl, c0, P, part, lincomb_dot_chunks(g), err);
+  const int ntile = (2 * g.nint + kLinTN - 1) / kLinTN;
+  const CUtensorMap mCh = rows_map(chi, kp, ny, kp, TM), mCl = rows_map(clo, kp, ny, kp, TM);
+  const CUtensorMap mUh = rows_map(uth, kp, 2 * g.ld, kp, kLinTN), mUl = rows_map(utl, kp, 2 * g.ld, kp, kLinTN);
+  launch("lincomb", 32, k_lincomb_tc, dim3((ny + TM - 1) / TM, ntile), dim3(256), lincomb_tc_smem(), st, mCh, mCl, mUh, mUl, g, Y, ny, kp,
+         c0, P, part, lincomb_dot_chunks(g), err);
   WDF_CUDA_TRY(cudaGetLastError());
 }
 

@@ -6,8 +6,10 @@
   occupied orbitals so that the FP64 oracle finishes in about a minute). Every precision form is
   compared element by element with the oracle on drho and chi0bar phi: the plain FP64 form at
   cg_tol 1e-12 and the mixed forms at cg_tol 1e-10, all held to 1e-8 relative (largest deviation
-  over the largest magnitude). The measured errors are written to the file named by the
-  environment variable WDF_PARITY_REPORT when it is set.
+  over the largest magnitude); at the benchmark's cg_tol 1e-8 every form is held to 1e-6 (the
+  error is the residual tolerance times the conditioning of the shifted operators). The
+  measured errors are written to the file named by the environment variable WDF_PARITY_REPORT
+  when it is set.
 * The full precision system (128 atoms, 512 projectors, 256 occupied orbitals), where the oracle
   would need hours: properties of chi0bar that hold at any size on the FP64 result (symmetry and
   negative semidefiniteness of <phi_a, chi0bar phi_b>, no G = 0 density component), and, as an
@@ -46,8 +48,9 @@ def reduced():
     return s, phi, ref
 
 
-@pytest.mark.parametrize("prec,cg_tol", [("fp64", 1e-12), ("mixed", 1e-10), ("mixed_df", 1e-10)])
-def test_reduced_precision_system_matches_oracle(reduced, prec, cg_tol):
+@pytest.mark.parametrize("prec,cg_tol,bar", [("fp64", 1e-12, 1e-8), ("mixed", 1e-10, 1e-8), ("mixed_df", 1e-10, 1e-8),
+                                              ("fp64", 1e-8, 1e-6), ("mixed", 1e-8, 1e-6), ("mixed_df", 1e-8, 1e-6)])
+def test_reduced_precision_system_matches_oracle(reduced, prec, cg_tol, bar):
     s, phi, ref = reduced
     assert s.npw_h == 23149 and tuple(s.grid) == (96, 96, 96)
     with wdf.Context(s, precision=prec, cg_tol=cg_tol, gs_tol=1e-11) as c:
@@ -59,8 +62,8 @@ def test_reduced_precision_system_matches_oracle(reduced, prec, cg_tol):
         with open(path, "a") as f:
             f.write(json.dumps({"system": "precision_reduced", "precision": prec, "cg_tol": cg_tol, "drho_rel_err": e_drho,
                                 "out_rel_err": e_out, "max_residual": st.max_residual}) + "\n")
-    assert e_drho <= 1e-8, prec
-    assert e_out <= 1e-8, prec
+    assert e_drho <= bar, prec
+    assert e_out <= bar, prec
 
 
 @pytest.fixture(scope="module")
