@@ -1,12 +1,12 @@
 // Fifth-generation tensor core primitives (sm_100 family: tcgen05, TMEM, mbarrier) as inline PTX.
 //
-// Operand tiles live in shared memory in the K-major, 128-byte-swizzled layout: a row holds 32
-// FP32 values (128 bytes) of consecutive K; eight rows form a 1024-byte atom in which the 16-byte
-// chunk c of row r sits at chunk position c XOR (r mod 8); atoms follow each other along M/N. The
-// matrix descriptor gives the start address, the 1024-byte stride between atoms and the swizzle
-// mode; one MMA consumes 8 TF32 values of K (32 bytes), so consecutive K steps advance the start
-// address by 32 bytes inside the atom. Accumulators live in tensor memory (TMEM): for M = 128 row
-// i of D is TMEM lane i and column j is TMEM column j (FP32).
+// Operand tiles live in shared memory in the K-major, 64-byte-swizzled layout that the tensor
+// memory access unit writes: a row holds 16 FP32 values of consecutive K; eight rows form a
+// 512-byte atom in which the 16-byte chunks of a row are permuted by the row index; atoms follow
+// each other along M/N. The matrix descriptor gives the start address, the stride between atoms
+// and the swizzle mode; one MMA consumes 8 TF32 values of K (32 bytes), so consecutive K steps
+// advance the start address by 32 bytes inside the atom. Accumulators live in tensor memory
+// (TMEM): for M = 128 row i of D is TMEM lane i and column j is TMEM column j (FP32).
 #pragma once
 
 #include <cstdint>
@@ -15,23 +15,6 @@ namespace wdf {
 namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of the 16-byte chunk c (0..7) of row r in a swizzled K-major region
-__host__ __device__ __forceinline__ int swz_off(int r, int c) { return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4); }
-
-// shared-memory matrix descriptor: K-major, SWIZZLE_128B, stride 1024 B between 8-row atoms
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
-  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;           // leading byte offset (16 B; unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;           // descriptor version of the sm_100 family
-  d |= (uint64_t)2 << 61;           // 128-byte swizzle
-  return d;
-}
-
-// 64-byte-swizzled K-major rows (16 FP32 values): 16-byte chunk c (0..3) of row r sits at chunk
-// position c XOR ((r / 2) mod 4) inside its 8-row, 512-byte atom
-__host__ __device__ __forceinline__ int swz64_off(int r, int c) { return (r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r >> 1) & 3)) << 4); }
 
 // shared-memory matrix descriptor: K-major, SWIZZLE_64B, stride 512 B between 8-row atoms
 __device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
@@ -42,13 +25,6 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
   d |= (uint64_t)4 << 61;           // 64-byte swizzle
   return d;
 }
-
-// 16-byte asynchronous global -> shared copy (cp.async, L2 only); bytes < 16 zero-fills the rest
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
