@@ -449,7 +449,7 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->ml64,      &c->ml32,      &c->mlw64,   &c->krow,     &c->rr_ref,  &c->it_ref,  &c->nfb,
                   &c->mlsums,    &c->mlwraw,    &c->tcU,     &c->tcUt,     &c->tcC,     &c->tcerr,
                   &c->wp_phi,    &c->wp_x,      &c->wp_y,    &c->wp_vx,    &c->wp_S,    &c->wp_coef,
-                  &c->uop_in,    &c->uop_out,   &c->orbfields, &c->ones64,  &c->onesdf};
+                  &c->uop_in,    &c->uop_out,   &c->orbfields, &c->ones64,  &c->onesdf,  &c->pnorm};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {

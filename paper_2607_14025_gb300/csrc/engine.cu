@@ -637,7 +637,8 @@ void sternheimer_solve(wdf_ctx *c, const cplx<double> *b, cplx<double> *x, const
 // Stages S2, S3, S7, S8 in R (FP64 or double-float); xp: np2 rows of v^1/2 phi (FP64). Results
 // (np2 rows, FP64) go to ou = v^1/2 drho and dr = drho.
 template <typename R>
-static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, cplx<double> *ou, cplx<double> *dr, SolveStats &ss) {
+static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, const std::vector<char> &zero, cplx<double> *ou,
+                        cplx<double> *dr, SolveStats &ss) {
   constexpr bool DF = std::is_same<R, df64>::value;
   const Geo &g = c->geo;
   cudaStream_t st = c->st;
@@ -715,12 +716,13 @@ static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, cplx<do
       launch_lincomb<R>(g, bR, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
       if constexpr (DF) from_df(c, b, bR, ns);
     }
-    if ((npert & 1) && pp1 == npp) {
-      // the phantom partner of the last perturbation: its right-hand side is FFT rounding noise,
-      // set it to exactly zero so that its solves are skipped
-      const size_t row = sizeof(cplx<double>) * g.ld;
-      WDF_CUDA_TRY(cudaMemset2DAsync(b + ((size_t)2 * (npp - 1 - pp0) * nocc + 1) * g.ld, 2 * row, 0, row, nocc, st));
-    }
+    // a perturbation that is zero (and the phantom partner of an odd last one) has a right-hand
+    // side of FFT rounding noise from its Gamma partner: set it to exactly zero so that its
+    // solves are skipped and its response is zero
+    const size_t row = sizeof(cplx<double>) * g.ld;
+    for (int p = 2 * pp0; p < 2 * pp1; ++p)
+      if (p >= npert || zero[p])
+        WDF_CUDA_TRY(cudaMemset2DAsync(b + ((size_t)2 * (p / 2 - pp0) * nocc + (p & 1)) * g.ld, 2 * row, 0, row, nocc, st));
     std::vector<int> vidx(ns);
     for (int s = 0; s < ns; ++s) vidx[s] = (s / 2) % nocc;
     sternheimer_solve(c, b, x, vidx.data(), ns, sc);
@@ -807,8 +809,16 @@ void chi0_apply_internal(wdf_ctx *c, const cplx<double> *phi, int npert, cplx<do
   c->chi_out.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
   c->chi_drho.ensure(sizeof(cplx<double>) * (size_t)np2 * g.ld);
   cplx<double> *dr = c->chi_drho.as<cplx<double>>(), *ou = c->chi_out.as<cplx<double>>();
-  if (c->opt.precision == WDF_MIXED_DF) chi0_stages<df64>(c, xp, npert, ou, dr, ss);
-  else chi0_stages<double>(c, xp, npert, ou, dr, ss);
+  // perturbations that are exactly zero
+  std::vector<char> zero(npert, 0);
+  {
+    c->pnorm.ensure(sizeof(double) * (size_t)npert);
+    dots<double>(c, xp, xp, npert, c->pnorm.as<double>());
+    const std::vector<double> n2 = to_host(c, c->pnorm.as<double>(), npert);
+    for (int p = 0; p < npert; ++p) zero[p] = n2[p] == 0.0;
+  }
+  if (c->opt.precision == WDF_MIXED_DF) chi0_stages<df64>(c, xp, npert, zero, ou, dr, ss);
+  else chi0_stages<double>(c, xp, npert, zero, ou, dr, ss);
   const size_t nb = sizeof(cplx<double>) * (size_t)npert * g.ld;
   WDF_CUDA_TRY(cudaMemcpyAsync(out, ou, nb, cudaMemcpyDeviceToDevice, st));
   if (drho) WDF_CUDA_TRY(cudaMemcpyAsync(drho, dr, nb, cudaMemcpyDeviceToDevice, st));

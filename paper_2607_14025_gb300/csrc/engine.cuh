@@ -100,6 +100,7 @@ struct wdf_ctx {
   wdf::DBuf mlsums, mlwraw;
   wdf::DBuf wp_phi, wp_x, wp_y, wp_vx, wp_S, wp_coef;  // wdf_apply_wp
   wdf::DBuf uop_in, uop_out;                           // wdf_davidson: the caller's operator's in / out
+  wdf::DBuf pnorm;                      // squared norms of a block's perturbations
   wdf::DBuf orbfields, ones64, onesdf;  // orbital sum by G2R: one pair's real-space fields per orbital; psi = 1 grids
   bool collect = false;
   wdf::DBuf rb, rx, rr, rAx, rwork;        // refinement: b, x, r, A x (FP64), FP32 staging
