@@ -11,9 +11,12 @@ CG workspace); one step is one pass of the whole hot path over one chunk: wdf_pd
 and the Rayleigh-Ritz step of PDEP (subspace matrix, FP64 eigensolve, Ritz residuals). Steps
 cycle through the chunks, so 8 steps cover the 512-perturbation block.
 
-Beside it, in the same line: the plain FP64 GPU form on a sample of the same block (the
-metric's "vs FP64 GPU"), the medium configuration (64^3, 64 orbitals, 128 perturbations per
-step) as a secondary figure, and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+The inner CG uses the learned preconditioner (the MLP scale on TPA, with TPA as the fallback of a
+stalling solve), trained before the timed region on converged solves of 8 seeded systems of the
+96^3 learned family (the same grid and basis with 16 orbitals). Beside it, in the same line: the
+same steps with TPA alone, the plain FP64 GPU form on a sample of the same block (the metric's
+"vs FP64 GPU"), the medium configuration (64^3, 64 orbitals, 128 perturbations per step, TPA) as a
+secondary figure, and the FP64 CPU oracle on a bounded sample (cpu_baseline).
 
 Timing: W warm-up steps, then K steps bracketed by barriers and device synchronisation, CUDA events
 on the library's stream; L2 is flushed (256 MiB write) before every step and the step's working
@@ -411,11 +414,15 @@ def run_gpu(args):
             lam_h, vec_h, st_h = step(chunks_h[i % nch])
         torch.cuda.synchronize(dev)
         ms_e2e = 1e3 * (time.perf_counter() - t0) / n_e2e
-    learned_line = None
-    if args.precond == "tpa" and args.with_learned and world == 1:
-        # the same steps with the learned preconditioner (trained here, not timed), same protocol,
-        # one pass over the block's chunks
-        info = train_learned()
+    other_line = None
+    if args.with_other and world == 1:
+        # the same steps with the other preconditioner (the learned one trained here, not timed),
+        # same protocol, one pass over the block's chunks
+        if args.precond == "tpa":
+            info = train_learned()
+        else:
+            ctx.set_model(None)
+            info = None
         nl = max(1, min(args.steps, nch))
         with torch.cuda.stream(stream):
             for i in range(args.warmup):
@@ -431,9 +438,11 @@ def run_gpu(args):
             torch.cuda.synchronize(dev)
         ms_l = sum(a.elapsed_time(b) for a, b in evl) / nl
         dl = stl.as_dict()
-        learned_line = {"value": job_throughput(world, dl["nsolve"], ms_l), "unit": UNIT, "ms_per_step": ms_l, "steps": nl,
-                        "cg_iters_per_solve": dl["cg_iters"] / max(1, dl["nsolve"]), "cg_iters_max": dl["cg_iters_max"],
-                        "max_residual": dl["max_residual"], "fallbacks_per_step": dl["fallbacks"], "training": info}
+        other_line = {"value": job_throughput(world, dl["nsolve"], ms_l), "unit": UNIT, "ms_per_step": ms_l, "steps": nl,
+                      "cg_iters_per_solve": dl["cg_iters"] / max(1, dl["nsolve"]), "cg_iters_max": dl["cg_iters_max"],
+                      "max_residual": dl["max_residual"], "fallbacks_per_step": dl["fallbacks"]}
+        if info:
+            other_line["training"] = info
     ctx.close()
     fp64_line = None
     if args.fp64_npert > 0:
@@ -494,9 +503,9 @@ def run_gpu(args):
     if secondary:
         line["medium"] = secondary
     if train_info:
-        line["learned_preconditioner"] = train_info
-    if learned_line:
-        line["learned_preconditioner"] = learned_line
+        line["learned_preconditioner"] = {"training": train_info, "fallbacks_per_step": stats[-1]["fallbacks"]}
+    if other_line:
+        line["learned_preconditioner" if args.precond == "tpa" else "tpa_preconditioner"] = other_line
     if args.cpu_baseline:
         o = OracleSample(wl)
         dt, nv, it = o.run()
@@ -684,10 +693,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true", help="one warm step, then one step between "
                     "cudaProfilerStart/Stop for ncu --profile-from-start off; no timing line")
-    ap.add_argument("--precond", choices=["tpa", "learned"], default="tpa",
-                    help="learned: train the MLP preconditioner on other seeds of the family first (not timed)")
-    ap.add_argument("--no-learned", dest="with_learned", action="store_false",
-                    help="skip the extra timing of the learned preconditioner after the TPA headline")
+    ap.add_argument("--precond", choices=["tpa", "learned"], default="learned",
+                    help="learned (default): train the MLP preconditioner on seeded systems of the family first (not "
+                         "timed; for the precision workload on the 96^3 learned family), TPA as fallback; tpa: TPA alone")
+    ap.add_argument("--no-other-precond", dest="with_other", action="store_false",
+                    help="skip the extra timing of the other preconditioner (TPA when the headline is learned)")
     ap.add_argument("--workload", choices=["precision", "precision_small", "medium", "batching", "learned"], default="precision",
                     help="precision (the headline: 96^3, 256 orbitals, 512 perturbations in chunks of 64); precision_small "
                          "(its 96^3 layout with 16 orbitals, for small-case profiler captures); medium "
