@@ -160,6 +160,16 @@ int wdf_get_orbitals(wdf_ctx *ctx, double *eps, double *psi, int mem);
  * in, out: [nvec][npw_h] complex, host or device per mem; out may alias in. */
 int wdf_apply_hamiltonian(wdf_ctx *ctx, int nvec, const double *in, double *out, int mem);
 
+/* Apply the operator of the Sternheimer equations of Sec. 2.1, A_v = H - eps_v + alpha P (P the
+ * projector on the occupied space, alpha the shift of wdf_options), to nvec half-sphere vectors,
+ * vector k with v = vidx[k], in the precision the library computes residuals b - A x in: FP64
+ * for WDF_FP64 and WDF_MIXED; double-float (about 48 significant bits, the projections on
+ * [beta; psi] on the tensor cores by exact integer digits) for WDF_MIXED_DF.
+ * vidx: [nvec] (host), each in [0, nocc). in, out: [nvec][npw_h] complex, host or device per
+ * mem; out may alias in. Errors: WDF_EINVAL (bad sizes, NULL buffers, vidx out of range),
+ * WDF_ETIMEOUT (a tensor-core kernel gave up waiting; out is then undefined). */
+int wdf_apply_sternheimer_operator(wdf_ctx *ctx, int nvec, const int32_t *vidx, const double *in, double *out, int mem);
+
 /* Solve the Sternheimer equations of Sec. 2.1 for nsolve right-hand sides:
  * (H - eps_v + alpha P) x_k = rhs_k with v = vidx[k], P the projector on the occupied space,
  * to ||rhs_k - A x_k|| <= cg_tol ||rhs_k||. For rhs_k orthogonal to the occupied space this is

@@ -268,6 +268,7 @@ void setup_body(wdf_ctx *c, const wdf_system *sys) {
   set_chol_inv_limits(kCholMax);
   set_mlp_limits();
   if (tc_enabled()) set_tc_limits();
+  if (oz_enabled()) set_oz_limits();
 
   // local potential
   c->vloc64.ensure(sizeof(double) * c->ngrid);
@@ -449,7 +450,9 @@ void wdf_destroy(wdf_ctx *c) {
                   &c->ml64,      &c->ml32,      &c->mlw64,   &c->krow,     &c->rr_ref,  &c->it_ref,  &c->nfb,
                   &c->mlsums,    &c->mlwraw,    &c->tcU,     &c->tcUt,     &c->tcC,     &c->tcerr,
                   &c->wp_phi,    &c->wp_x,      &c->wp_y,    &c->wp_vx,    &c->wp_S,    &c->wp_coef,
-                  &c->uop_in,    &c->uop_out,   &c->orbfields, &c->ones64,  &c->onesdf,  &c->pnorm};
+                  &c->uop_in,    &c->uop_out,   &c->orbfields, &c->ones64,  &c->onesdf,  &c->pnorm,
+                  &c->ozU,       &c->ozUe,      &c->ozUt,    &c->ozUte,    &c->ozPt,    &c->ozPte,   &c->ozX,
+                  &c->ozXe,      &c->ozC,       &c->ozCe};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t e : c->prof.ev) (void)cudaEventDestroy(e);
   for (wdf_ctx::Cg *w : {&c->cg64, &c->cg32, &c->cgdf}) {
@@ -482,6 +485,24 @@ int wdf_apply_hamiltonian(wdf_ctx *c, int nvec, const double *in, double *out, i
     cplx<double> *X = read_in(c, c->ext_in, c->xpert, in, nvec, mem);
     c->outi.ensure(sizeof(cplx<double>) * (size_t)nvec * c->geo.ld);
     apply_operator<double>(c, X, c->outi.as<cplx<double>>(), nvec, nullptr, false);
+    write_out(c, c->ext_out, c->outi.as<cplx<double>>(), nvec, out, mem);
+    WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
+    return WDF_OK;
+  });
+}
+
+int wdf_apply_sternheimer_operator(wdf_ctx *c, int nvec, const int32_t *vidx, const double *in, double *out, int mem) {
+  if (!c) return WDF_EINVAL;
+  return guarded(c, [&] {
+    check_mem(mem);
+    if (nvec < 0 || (nvec > 0 && (!vidx || !in || !out))) throw ApiFailure(WDF_EINVAL, "bad nvec or NULL buffer");
+    for (int s = 0; s < nvec; ++s)
+      if (vidx[s] < 0 || vidx[s] >= c->nocc) throw ApiFailure(WDF_EINVAL, "vidx out of range");
+    if (nvec == 0) return WDF_OK;
+    cplx<double> *X = read_in(c, c->ext_in, c->xpert, in, nvec, mem);
+    c->outi.ensure(sizeof(cplx<double>) * (size_t)nvec * c->geo.ld);
+    std::vector<int> v(vidx, vidx + nvec);
+    apply_sternheimer_operator(c, X, c->outi.as<cplx<double>>(), v.data(), nvec);
     write_out(c, c->ext_out, c->outi.as<cplx<double>>(), nvec, out, mem);
     WDF_CUDA_TRY(cudaStreamSynchronize(c->st));
     return WDF_OK;

@@ -211,6 +211,43 @@ static void gram(wdf_ctx *c, const cplx<T> *A, int na, const cplx<T> *B, int nb,
   launch_gram<T>(c->geo, A, na, B, nb, out, ldo, w, cap, c->st);
 }
 
+// digit matrix of rows x K values in (dig, ex), grown on demand
+static OzMat oz_mat(DBuf &dig, DBuf &ex, int rows, int K) {
+  OzMat m;
+  m.rows = rows;
+  m.kpad = oz_kpad(K);
+  m.plane = (size_t)rows * m.kpad;
+  dig.ensure(sizeof(uint16_t) * OZ_DIGITS * std::max<size_t>(m.plane, 1));
+  ex.ensure(sizeof(int) * std::max(rows, 1));
+  m.dig = dig.as<uint16_t>();
+  m.ex = ex.as<int>();
+  return m;
+}
+
+// Low-rank part on the tensor cores in double-float: Y = c0 Y + Bt (d o (A^T X)) with A the
+// weighted rows j0 .. j0 + na - 1 of U (digits c->oz_u) and Bt the matching digits of U^T (all
+// rows of U, or the orbital rows). S (na x n doubles, row stride n) receives the projections.
+static void oz_lowrank(wdf_ctx *c, int j0, int na, const OzMat &Bt, const cplx<df64> *X, cplx<df64> *Y, int n, const double *d, float c0,
+                       double *S) {
+  const Geo &g = c->geo;
+  const int kf = 2 * g.nint;
+  const OzMat A = c->oz_u.sub(j0, na);
+  // the vectors' digits in chunks of at most 8,192 rows (5.3 GB of digits at 96^3)
+  const int chunk = std::min(n, 8192);
+  for (int s0 = 0; s0 < n; s0 += chunk) {
+    const int ns = std::min(chunk, n - s0);
+    const OzMat Xd = oz_mat(c->ozX, c->ozXe, ns, kf);
+    launch_oz_rows_df(g, X + (size_t)s0 * g.ld, ns, false, Xd, c->st);
+    const size_t need = oz_gram_work_doubles(na, ns, kf);
+    c->gramw.ensure(sizeof(double) * std::max<size_t>(need, 1));
+    launch_oz_gram(A, Xd, kf, S + s0, n, c->gramw.as<double>(), c->gramw.cap / sizeof(double), c->tcerr.as<int>(), c->st);
+  }
+  const OzMat Cd = oz_mat(c->ozC, c->ozCe, n, na);
+  launch_oz_cols(S, (size_t)n, na, n, d, Cd, c->st);
+  OzMat B = Bt;
+  launch_oz_lincomb(Cd, B, na, reinterpret_cast<df64 *>(Y), (size_t)2 * g.ld, c0, c->tcerr.as<int>(), c->st);
+}
+
 // per-vector inner products <A_s, B_s> into a device array (n doubles)
 template <typename T>
 static void dots(wdf_ctx *c, const cplx<T> *A, const cplx<T> *B, int n, double *out) {
@@ -281,6 +318,13 @@ void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const doubl
     launch_zpass_r2g<T>(f, EPI_HSHIFT, cb, ns, ea, c->st);
   }
   const int M = c->nproj + (with_alpha ? c->nocc : 0);
+  if constexpr (std::is_same<T, df64>::value) {
+    if (M > 0 && c->oz_on) {
+      w.S.ensure(sizeof(double) * (size_t)M * n);
+      oz_lowrank(c, 0, M, c->oz_ut, X, Y, n, c->lrd.as<double>(), 1.f, w.S.as<double>());
+      return;
+    }
+  }
   if (M > 0) {
     w.S.ensure(sizeof(double) * (size_t)M * n);
     gram<T>(c, Prec<T>::U(c), M, X, n, w.S.as<double>(), n);
@@ -490,6 +534,32 @@ static void cg_solve(wdf_ctx *c, const cplx<T> *b, cplx<T> *x, int n, int maxite
   iters.resize(n);
   WDF_CUDA_TRY(cudaMemcpyAsync(iters.data(), ii + n, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
   WDF_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void apply_sternheimer_operator(wdf_ctx *c, const cplx<double> *X, cplx<double> *Y, const int *vidx_host, int n) {
+  if (n <= 0) return;
+  const Geo &g = c->geo;
+  cudaStream_t st = c->st;
+  c->vidx_dev.ensure(sizeof(int) * n);
+  c->shift.ensure(sizeof(double) * n);
+  WDF_CUDA_TRY(cudaMemcpyAsync(c->vidx_dev.p, vidx_host, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  launch("gather_shift", 0, k_gather_shift, dim3((n + 127) / 128), dim3(128), 0, st, c->vidx_dev.as<int>(), c->eps_dev.as<double>(),
+         c->shift.as<double>(), n);
+  WDF_CUDA_TRY(cudaGetLastError());
+  if (c->opt.precision == WDF_MIXED_DF) {
+    const size_t vb = sizeof(cplx<double>) * (size_t)n * g.ld;
+    c->dfa.ensure(vb);
+    c->dfb.ensure(vb);
+    to_df(c, c->dfa.as<cplx<df64>>(), X, n);
+    apply_operator<df64>(c, c->dfa.as<cplx<df64>>(), c->dfb.as<cplx<df64>>(), n, c->shift.as<double>(), true);
+    from_df(c, Y, c->dfb.as<cplx<df64>>(), n);
+  } else {
+    apply_operator<double>(c, X, Y, n, c->shift.as<double>(), true);
+  }
+  int terr = 0;
+  WDF_CUDA_TRY(cudaMemcpyAsync(&terr, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WDF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (terr) throw ApiFailure(WDF_ETIMEOUT, "a kernel gave up waiting for its MMAs or bulk copies");
 }
 
 // FP64 outer loop: r = b - A x in FP64, inner solve A d = r (FP64 or FP32), x += d.
@@ -712,8 +782,17 @@ static void chi0_stages(wdf_ctx *c, const cplx<double> *xp64, int npert, const s
       ea.scale = R(1.0 / (double)ngrid);
       launch_zpass_r2g<R>(f, EPI_STORE, cb, ns, ea, st);
       w.S.ensure(sizeof(double) * (size_t)nocc * ns);
-      gram<R>(c, psi, nocc, bR, ns, w.S.as<double>(), ns);
-      launch_lincomb<R>(g, bR, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
+      bool done = false;
+      if constexpr (DF) {
+        if (c->oz_on) {  // b = -(b - psi (psi^T b)) on the tensor cores
+          oz_lowrank(c, c->nproj, nocc, c->oz_pt, bR, bR, ns, nullptr, -1.f, w.S.as<double>());
+          done = true;
+        }
+      }
+      if (!done) {
+        gram<R>(c, psi, nocc, bR, ns, w.S.as<double>(), ns);
+        launch_lincomb<R>(g, bR, ns, psi, nocc, w.S.as<double>(), ns, nullptr, -1.0, st);
+      }
       if constexpr (DF) from_df(c, b, bR, ns);
     }
     // a perturbation that is zero (and the phantom partner of an odd last one) has a right-hand
@@ -1190,6 +1269,18 @@ void finish_setup(wdf_ctx *c) {
     launch_convert<double, df64>(g, c->vlocdf.as<df64>(), c->vloc64.as<double>(), c->ngrid, st);
     c->psirdf.ensure(sizeof(df64) * (size_t)nocc * c->ngrid);
     launch_convert<double, df64>(g, c->psirdf.as<df64>(), c->psir64.as<double>(), (size_t)nocc * c->ngrid, st);
+    // digits of the weighted rows of U (the Gram's A operand), of U^T over all rows and of psi^T
+    // over the orbital rows (the linear combinations' B operands), from the FP64 copy
+    c->oz_on = oz_enabled() && c->tc_on;
+    if (c->oz_on) {
+      const int kf = 2 * g.nint;
+      c->oz_u = oz_mat(c->ozU, c->ozUe, M, kf);
+      launch_oz_rows_f64(g, c->U64.as<cplx<double>>(), M, true, c->oz_u, st);
+      c->oz_ut = oz_mat(c->ozUt, c->ozUte, kf, M);
+      launch_oz_cols(c->U64.as<double>(), (size_t)2 * g.ld, M, kf, nullptr, c->oz_ut, st);
+      c->oz_pt = oz_mat(c->ozPt, c->ozPte, kf, nocc);
+      launch_oz_cols(c->U64.as<double>() + (size_t)c->nproj * 2 * g.ld, (size_t)2 * g.ld, nocc, kf, nullptr, c->oz_pt, st);
+    }
   }
   // the V_loc plane kernels of the inner CG and of the residuals: time the variants that exist
   // for this grid and keep the fastest

@@ -95,6 +95,12 @@ struct wdf_ctx {
   float *tc_uwl() const { return tcU.as<float>() + (size_t)(nproj + nocc) * 2 * geo.ld; }
   float *tc_uth() const { return tcUt.as<float>(); }
   float *tc_utl() const { return tcUt.as<float>() + (size_t)2 * geo.ld * wdf::tc_rows(nproj + nocc); }
+  // tensor-core double-float projections (exact integer digits): digits of the weighted rows of
+  // U, of U^T (all rows) and of psi^T (the orbital rows), and their exponents; workspaces for
+  // the digits of the vectors and of the coefficients
+  wdf::DBuf ozU, ozUe, ozUt, ozUte, ozPt, ozPte, ozX, ozXe, ozC, ozCe;
+  wdf::OzMat oz_u, oz_ut, oz_pt;
+  bool oz_on = false;
   bool has_model = false;
   // training-sample collection (wdf_model_add_solves): sums [3][nocc][ld] over converged solves
   wdf::DBuf mlsums, mlwraw;
@@ -121,6 +127,9 @@ namespace wdf {
 // operators (engine.cu)
 template <typename T>
 void apply_operator(wdf_ctx *c, const cplx<T> *X, cplx<T> *Y, int n, const double *shift, bool with_alpha);
+// A_v x = (H - eps_v + alpha P) x in the precision of the residuals (FP64, or double-float for
+// WDF_MIXED_DF); vidx_host: [n] orbital of each vector
+void apply_sternheimer_operator(wdf_ctx *c, const cplx<double> *X, cplx<double> *Y, const int *vidx_host, int n);
 
 struct SolveStats {
   long long iters = 0;

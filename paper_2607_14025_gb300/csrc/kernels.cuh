@@ -240,6 +240,38 @@ void launch_gram_tc(const Geo &g, const float *X, int nb, const float *uwh, cons
 void launch_lincomb_tc(const Geo &g, float *Y, int ny, const double *S, int ldc, const double *d, int na, float *chi, float *clo,
                        const float *uth, const float *utl, float c0, const float *P, double *part, int *err, cudaStream_t st);
 
+// double-float projections on the tensor cores by exact integer digits (oz_gemm.cu); on with the
+// tensor-core path unless WDF_NO_OZ is set in the environment
+constexpr int OZ_DIGITS = 7;  // digits of 7 bits per value: a 49-bit fixed-point copy of each row
+struct OzMat {
+  uint16_t *dig = nullptr;  // [OZ_DIGITS][plane] bf16 digits: row r at dig + t plane + r kpad
+  int *ex = nullptr;        // [rows] row exponents (every |value| < 2^ex)
+  int rows = 0, kpad = 0;   // kpad: allocated values per row (a multiple of 32)
+  size_t plane = 0;         // values between digit planes
+  OzMat sub(int r0, int nr) const {
+    OzMat m = *this;
+    m.dig += (size_t)r0 * kpad;
+    m.ex += r0;
+    m.rows = nr;
+    return m;
+  }
+};
+bool oz_enabled();
+int oz_kpad(int K);
+void set_oz_limits();
+// digits of rows of 2 N_int real values (complex rows of ld), times the Gamma-point weights when
+// weighted
+void launch_oz_rows_df(const Geo &g, const cplx<df64> *src, int rows, bool weighted, const OzMat &out, cudaStream_t st);
+void launch_oz_rows_f64(const Geo &g, const cplx<double> *src, int rows, bool weighted, const OzMat &out, cudaStream_t st);
+// digits of the transpose of src[j][c] (j < nj, c < ncol, row stride lds), row j scaled by d[j]
+void launch_oz_cols(const double *src, size_t lds, int nj, int ncol, const double *d, const OzMat &out, cudaStream_t st);
+size_t oz_gram_work_doubles(int na, int nb, int K);
+// out[j][s] (row stride ldo) = sum_k U[j][k] X[s][k] over K values
+void launch_oz_gram(const OzMat &U, const OzMat &X, int K, double *out, int ldo, double *work, size_t work_cap, int *err, cudaStream_t st);
+// Y[s][f] = c0 Y[s][f] + sum_j C[s][j] Ut[f][j] over K values of j (double-float Y, row stride ldy
+// double-floats; c0 in {-1, 0, 1})
+void launch_oz_lincomb(const OzMat &C, const OzMat &Ut, int K, df64 *Y, size_t ldy, float c0, int *err, cudaStream_t st);
+
 // symmetric eigensolver (cyclic Jacobi, parallel ordering) of an n x n matrix A (ld = n), FP64.
 // On exit w holds eigenvalues ascending and V[i * n + k] the i-th component of eigenvector k.
 // polls of the cooperative eigensolver's grid barrier before it gives up and flags the error

@@ -446,7 +446,7 @@ size_t lincomb_tc_smem() {
 }  // namespace
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda)
-static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {

@@ -141,6 +141,7 @@ def load(path: str = LIB_PATH):
         "wdf_get_orbitals": (I, [P, P, P, I]),
         "wdf_apply_hamiltonian": (I, [P, I, P, P, I]),
         "wdf_sternheimer": (I, [P, I, P, P, P, I, P]),
+        "wdf_apply_sternheimer_operator": (I, [P, I, P, P, P, I]),
         "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
         "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
         "wdf_apply_hamiltonian_noalloc": (I, [P, I, P, P]),
@@ -379,6 +380,19 @@ class Context:
     def set_wait_limit(self, polls: int):
         """Polls of the software device waits before they give up (wdf_set_wait_limit; 0: default)."""
         self._check(self._lib.wdf_set_wait_limit(self._ctx, int(polls)))
+
+    def apply_sternheimer_operator(self, vidx, x):
+        """(H - eps_v + alpha P) x, vector k with v = vidx[k], in the residuals' precision."""
+        keep: list = []
+        v = np.ascontiguousarray(vidx, dtype=np.int32)
+        x2 = x if (_is_torch(x) and x.is_cuda) else np.atleast_2d(x)
+        p, mem = _ptr_in(x2, np.complex128, keep)
+        n = x2.shape[0]
+        if v.shape[0] != n:
+            raise ValueError("one orbital index per vector")
+        out, op = self._out_like(x2, n)
+        self._check(self._lib.wdf_apply_sternheimer_operator(self._ctx, n, v.ctypes.data, p, op, mem))
+        return out
 
     def sternheimer(self, vidx, rhs):
         keep: list = []
