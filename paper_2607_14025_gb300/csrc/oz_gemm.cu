@@ -69,7 +69,7 @@ struct OzArgs {
   int rowsA, rowsB;    // valid rows of A (M side) and B (N side)
   int tilesA, tilesB;  // tiles of 128 A rows and 32 B rows
   int groupA;          // A tiles per raster group (consecutive CTAs walk B within a group)
-  int nst, per;        // K stages in all, stages per split
+  int nst, per, nsplit;  // K stages in all, stages per split, splits
   const int *eA, *eB;  // row exponents
   double *out;         // gram: out[a][b] (split partials at + z split_stride)
   int ldo;
@@ -114,6 +114,27 @@ __device__ __forceinline__ df64 df_of_int(int v) {
   return df_two_sum((float)(v - lo), (float)lo);
 }
 
+// work item -> (A tile, B tile, K split): items enumerate tiles x splits; within a split a group
+// of groupA A tiles walks every B tile (consecutive items share operands in L2)
+struct OzItem {
+  int a0, b0, z, c0, n;
+};
+__device__ __forceinline__ OzItem oz_item(const OzArgs &p, int item) {
+  const int tiles = p.tilesA * p.tilesB;
+  const int z = item / tiles, lin = item % tiles;
+  const int gsz = p.groupA * p.tilesB, grp = lin / gsz, ingrp = lin % gsz;
+  const int ga = min(p.groupA, p.tilesA - grp * p.groupA);
+  OzItem it;
+  it.a0 = (grp * p.groupA + ingrp % ga) * OZ_M;
+  it.b0 = (ingrp / ga) * OZ_NB;
+  it.z = z;
+  it.c0 = z * p.per;
+  it.n = max(0, min(p.nst, it.c0 + p.per) - it.c0);
+  return it;
+}
+
+// persistent: CTA c takes items c, c + gridDim.x, ...; the stage ring and the chain counter run on
+// across items, so the epilogue of one item overlaps the MMAs of the next
 template <int T, int EPI>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                                                            OzArgs p) {
@@ -124,13 +145,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
   uint64_t *empty = full + C::STAGES, *chain = empty + C::STAGES, *tfree = chain + 2;
   uint32_t *slot = reinterpret_cast<uint32_t *>(tfree + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // grouped raster: a group of groupA A tiles walks every B tile
-  const int lin = blockIdx.x, gsz = p.groupA * p.tilesB, grp = lin / gsz, ingrp = lin % gsz;
-  const int ga = min(p.groupA, p.tilesA - grp * p.groupA);
-  const int ta = grp * p.groupA + ingrp % ga, tb = ingrp / ga;
-  const int a0 = ta * OZ_M, b0 = tb * OZ_NB;
-  const int c0 = blockIdx.z * p.per, n = max(0, min(p.nst, c0 + p.per) - c0);
-  const int nchains = (n + OZ_CHAIN - 1) / OZ_CHAIN;
+  const int nitems = p.tilesA * p.tilesB * p.nsplit;
   if (tid == 0) {
     for (int i = 0; i < C::STAGES; ++i) {
       tc::mbar_init(&full[i], 1);
@@ -150,101 +165,115 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
   bool fail = false;
   if (warp == 0) {
     if (lane == 0) {  // loads: A digit t into plane t, B digit u into block T - 1 - u
-      int issued = 0;
-      for (int i = 0; i < n; ++i) {
-        const int st = i % C::STAGES, k = i / C::STAGES;
-        if (k > 0 && !tc::mbar_wait(&empty[st], (k - 1) & 1, kWaitLimit)) {
-          fail = true;
-          break;
+      long g = 0;     // stages issued by this CTA
+      for (int item = blockIdx.x; item < nitems && !fail; item += gridDim.x) {
+        const OzItem it = oz_item(p, item);
+        for (int i = 0; i < it.n; ++i, ++g) {
+          const int st = (int)(g % C::STAGES);
+          const long k = g / C::STAGES;
+          if (k > 0 && !tc::mbar_wait(&empty[st], (uint32_t)((k - 1) & 1), kWaitLimit)) {
+            fail = true;
+            break;
+          }
+          unsigned char *S = sm + st * C::SB;
+          const int kx = (it.c0 + i) * OZ_KS;
+          mbar_expect_tx(&full[st], (uint32_t)C::SB);
+#pragma unroll
+          for (int t = 0; t < T; ++t) tma_load3d(S + t * C::AB, &mA, kx, it.a0, t, &full[st]);
+#pragma unroll
+          for (int u = 0; u < T; ++u) tma_load3d(S + T * C::AB + (T - 1 - u) * C::BB, &mB, kx, it.b0, u, &full[st]);
         }
-        unsigned char *S = sm + st * C::SB;
-        const int kx = (c0 + i) * OZ_KS;
-        mbar_expect_tx(&full[st], (uint32_t)C::SB);
-#pragma unroll
-        for (int t = 0; t < T; ++t) tma_load3d(S + t * C::AB, &mA, kx, a0, t, &full[st]);
-#pragma unroll
-        for (int u = 0; u < T; ++u) tma_load3d(S + T * C::AB + (T - 1 - u) * C::BB, &mB, kx, b0, u, &full[st]);
-        issued = i + 1;
       }
       // every copy issued lands before the block's shared memory goes away
-      for (int i = max(0, issued - C::STAGES); i < issued; ++i)
-        if (!tc::mbar_wait(&full[i % C::STAGES], (i / C::STAGES) & 1, kWaitLimit)) fail = true;
+      for (long i = max(0L, g - C::STAGES); i < g; ++i)
+        if (!tc::mbar_wait(&full[i % C::STAGES], (uint32_t)((i / C::STAGES) & 1), kWaitLimit)) fail = true;
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMAs
-      int issued = 0;
-      for (int i = 0; i < n; ++i) {
-        const int st = i % C::STAGES, k = i / C::STAGES, q = i / OZ_CHAIN, first = (i % OZ_CHAIN) == 0;
-        if (first && q >= 2 && !tc::mbar_wait(&tfree[q & 1], ((q - 2) >> 1) & 1, kWaitLimit)) {
-          fail = true;
-          break;
+      long g = 0;     // stages consumed
+      int q0 = 0;     // chains started by earlier items
+      for (int item = blockIdx.x; item < nitems && !fail; item += gridDim.x) {
+        const OzItem it = oz_item(p, item);
+        for (int i = 0; i < it.n; ++i, ++g) {
+          const int st = (int)(g % C::STAGES), q = q0 + i / OZ_CHAIN, first = (i % OZ_CHAIN) == 0;
+          const long k = g / C::STAGES;
+          if (first && q >= 2 && !tc::mbar_wait(&tfree[q & 1], ((q - 2) >> 1) & 1, kWaitLimit)) {
+            fail = true;
+            break;
+          }
+          if (!tc::mbar_wait(&full[st], (uint32_t)(k & 1), kWaitLimit)) {
+            fail = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t base = tc::smem_u32(sm + st * C::SB);
+          const uint32_t acc = tmem + (uint32_t)((q & 1) * 256);
+#pragma unroll
+          for (int ks = 0; ks < OZ_KS / 16; ++ks)
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+              mma_bf16(acc, tc::desc_sw64(base + t * C::AB + 32 * ks), tc::desc_sw64(base + T * C::AB + t * C::BB + 32 * ks),
+                       idesc_bf16(OZ_M, (T - t) * OZ_NB), (first && ks == 0 && t == 0) ? 0u : 1u);
+          tc::mma_commit(&empty[st]);
+          if ((i % OZ_CHAIN) == OZ_CHAIN - 1 || i == it.n - 1) tc::mma_commit(&chain[q & 1]);
         }
-        if (!tc::mbar_wait(&full[st], k & 1, kWaitLimit)) {
+        q0 += (it.n + OZ_CHAIN - 1) / OZ_CHAIN;
+      }
+      if (g > 0 && !tc::mbar_wait(&empty[(g - 1) % C::STAGES], (uint32_t)(((g - 1) / C::STAGES) & 1), kWaitLimit))
+        fail = true;  // the MMAs issued have finished with TMEM and shared memory
+    }
+  } else if (warp >= 4) {  // chains out of TMEM; each item's result after its last chain
+    const int qd = warp & 3, h = (warp - 4) >> 2;
+    const int ra = 32 * qd + lane;  // tile row (TMEM lane)
+    int q0 = 0;
+    for (int item = blockIdx.x; item < nitems && !fail; item += gridDim.x) {
+      const OzItem it = oz_item(p, item);
+      const int nchains = (it.n + OZ_CHAIN - 1) / OZ_CHAIN;
+      int ia[4][16];
+      float fa[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        ia[0][c] = ia[1][c] = ia[2][c] = ia[3][c] = 0;
+        fa[c] = 0.f;
+      }
+      for (int cc = 0; cc < nchains; ++cc) {
+        const int q = q0 + cc;
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&chain[q & 1], (q >> 1) & 1, kWaitLimit))) {
           fail = true;
           break;
         }
         tc::fence_after_sync();
-        const uint32_t base = tc::smem_u32(sm + st * C::SB);
-        const uint32_t acc = tmem + (uint32_t)((q & 1) * 256);
+        const uint32_t base = tmem + (uint32_t)((q & 1) * 256) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * h);
 #pragma unroll
-        for (int ks = 0; ks < OZ_KS / 16; ++ks)
+        for (int b = 0; b < T; ++b) {
+          constexpr float r7 = 1.0f / 128.0f;
+          const int gidx = T - 1 - b;
+          float v[16];
+          tc::tmem_ld16(base + (uint32_t)(b * OZ_NB), v);
+          if (gidx <= 3) {
 #pragma unroll
-          for (int t = 0; t < T; ++t)
-            mma_bf16(acc, tc::desc_sw64(base + t * C::AB + 32 * ks), tc::desc_sw64(base + T * C::AB + t * C::BB + 32 * ks),
-                     idesc_bf16(OZ_M, (T - t) * OZ_NB), (first && ks == 0 && t == 0) ? 0u : 1u);
-        tc::mma_commit(&empty[st]);
-        if ((i % OZ_CHAIN) == OZ_CHAIN - 1 || i == n - 1) tc::mma_commit(&chain[q & 1]);
-        issued = i + 1;
-      }
-      if (issued > 0 && !tc::mbar_wait(&empty[(issued - 1) % C::STAGES], ((issued - 1) / C::STAGES) & 1, kWaitLimit))
-        fail = true;  // the MMAs issued have finished with TMEM and shared memory
-    }
-  } else if (warp >= 4) {  // chains out of TMEM; the result at the end
-    const int qd = warp & 3, h = (warp - 4) >> 2;
-    const int ra = 32 * qd + lane;  // tile row (TMEM lane)
-    int ia[4][16];
-    float fa[16];
+            for (int c = 0; c < 16; ++c) ia[gidx][c] += __float2int_rn(v[c]);
+          } else {
+            float sc = 1.f;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      ia[0][c] = ia[1][c] = ia[2][c] = ia[3][c] = 0;
-      fa[c] = 0.f;
-    }
-    for (int q = 0; q < nchains; ++q) {
-      if (!__all_sync(0xffffffffu, tc::mbar_wait(&chain[q & 1], (q >> 1) & 1, kWaitLimit))) {
-        fail = true;
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t base = tmem + (uint32_t)((q & 1) * 256) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * h);
+            for (int e = 0; e < gidx; ++e) sc *= r7;
 #pragma unroll
-      for (int b = 0; b < T; ++b) {
-        constexpr float r7 = 1.0f / 128.0f;
-        const int g = T - 1 - b;
-        float v[16];
-        tc::tmem_ld16(base + (uint32_t)(b * OZ_NB), v);
-        if (g <= 3) {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) ia[g][c] += __float2int_rn(v[c]);
-        } else {
-          float sc = 1.f;
-#pragma unroll
-          for (int e = 0; e < g; ++e) sc *= r7;
-#pragma unroll
-          for (int c = 0; c < 16; ++c) fa[c] = __fmaf_rn(v[c], sc, fa[c]);
+            for (int c = 0; c < 16; ++c) fa[c] = __fmaf_rn(v[c], sc, fa[c]);
+          }
         }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tfree[q & 1]);
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tfree[q & 1]);
-    }
-    const int a = a0 + ra;
-    if (!fail && a < p.rowsA) {
+      q0 += nchains;
+      const int a = it.a0 + ra;
+      if (fail || a >= p.rowsA) continue;
       const int ea = p.eA[a];
       if constexpr (EPI == OZ_GRAM) {
-        double *o = p.out + (size_t)blockIdx.z * p.split_stride + (size_t)a * p.ldo;
+        double *o = p.out + (size_t)it.z * p.split_stride + (size_t)a * p.ldo;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int b = b0 + 16 * h + c;
+          const int b = it.b0 + 16 * h + c;
           if (b < p.rowsB) {
             const double v = (double)ia[0][c] + 0x1p-7 * (double)ia[1][c] + 0x1p-14 * (double)ia[2][c] + 0x1p-21 * (double)ia[3][c] +
                              (double)fa[c];
@@ -253,22 +282,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
         }
       } else {
         df64 *y = p.Y + (size_t)a * p.ldy;
+        const int bb = it.b0 + 16 * h;
+        df64 old[16];  // every load in flight before the arithmetic
+#pragma unroll
+        for (int c = 0; c < 16; ++c) old[c] = (p.c0 != 0.f && bb + c < p.rowsB) ? y[bb + c] : df64(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int b = b0 + 16 * h + c;
+          const int b = bb + c;
           if (b < p.rowsB) {
             df64 s = df_of_int(ia[0][c]);
-            df64 t1 = df_of_int(ia[1][c]), t2 = df_of_int(ia[2][c]), t3 = df_of_int(ia[3][c]);
+            const df64 t1 = df_of_int(ia[1][c]), t2 = df_of_int(ia[2][c]), t3 = df_of_int(ia[3][c]);
             s = s + df64(t1.hi * 0x1p-7f, t1.lo * 0x1p-7f);
             s = s + df64(t2.hi * 0x1p-14f, t2.lo * 0x1p-14f);
             s = s + df64(t3.hi * 0x1p-21f, t3.lo * 0x1p-21f);
             s = s + df64(fa[c], 0.f);
             const int e = ea + p.eB[b] - 14;
             s = df64(ldexpf(s.hi, e), ldexpf(s.lo, e));
-            if (p.c0 != 0.f) {
-              const df64 old = y[b];
-              s = s + (p.c0 > 0.f ? old : -old);
-            }
+            if (p.c0 != 0.f) s = s + (p.c0 > 0.f ? old[c] : -old[c]);
             y[b] = s;
           }
         }
@@ -318,32 +348,47 @@ __device__ __forceinline__ void put_bf16x2(uint16_t *dst, float a, float b) {
 
 // digits of the rows of a complex matrix (K = 2 N_int real values per row, src[r][ld] complex),
 // times the Gamma-point weights (1 on the first len0 elements, 2 on the rest) when weighted;
-// one block of 256 threads per row. dig: [T][rows][kpad], ex: [rows].
+// one block of 256 threads per row, four elements per thread and iteration with their loads
+// issued together. dig: [T][rows][kpad], ex: [rows].
 template <int T>
 __global__ void __launch_bounds__(256) k_oz_rows_df(const cplx<df64> *__restrict__ src, int ld, int nint, int len0, bool weighted,
                                                     uint16_t *__restrict__ dig, int kpad, size_t plane, int *__restrict__ ex) {
+  constexpr int U = 4;
   const int r = blockIdx.x;
   const cplx<df64> *row = src + (size_t)r * ld;
+  const cplx<df64> zero = mkc<df64>(df64(0.f, 0.f), df64(0.f, 0.f));
   float m = 0.f;
-  for (int e = threadIdx.x; e < nint; e += 256) {
-    const cplx<df64> v = row[e];
-    const float w = (weighted && e >= len0) ? 2.f : 1.f;
-    m = fmaxf(m, w * fmaxf(fabsf(v.x.hi), fabsf(v.y.hi)));
+  for (int e0 = threadIdx.x; e0 < nint; e0 += 256 * U) {
+    cplx<df64> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = e0 + 256 * u < nint ? row[e0 + 256 * u] : zero;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float w = (weighted && e0 + 256 * u >= len0) ? 2.f : 1.f;
+      m = fmaxf(m, w * fmaxf(fabsf(v[u].x.hi), fabsf(v[u].y.hi)));
+    }
   }
   m = block_max256(m);
   const int E = oz_exponent(m);
   if (threadIdx.x == 0) ex[r] = E;
   const int sh = 7 * T - E;
-  for (int e = threadIdx.x; e < nint; e += 256) {
-    const cplx<df64> v = row[e];
-    const int sw = sh + ((weighted && e >= len0) ? 1 : 0);
-    const long long Ix = __float2ll_rn(ldexpf(v.x.hi, sw)) + __float2ll_rn(ldexpf(v.x.lo, sw));
-    const long long Iy = __float2ll_rn(ldexpf(v.y.hi, sw)) + __float2ll_rn(ldexpf(v.y.lo, sw));
-    float dx[T], dy[T];
-    oz_digits<T>(Ix, dx);
-    oz_digits<T>(Iy, dy);
+  for (int e0 = threadIdx.x; e0 < nint; e0 += 256 * U) {
+    cplx<df64> v[U];
 #pragma unroll
-    for (int t = 0; t < T; ++t) put_bf16x2(dig + t * plane + (size_t)r * kpad + 2 * e, dx[t], dy[t]);
+    for (int u = 0; u < U; ++u) v[u] = e0 + 256 * u < nint ? row[e0 + 256 * u] : zero;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + 256 * u;
+      if (e >= nint) break;
+      const int sw = sh + ((weighted && e >= len0) ? 1 : 0);
+      const long long Ix = __float2ll_rn(ldexpf(v[u].x.hi, sw)) + __float2ll_rn(ldexpf(v[u].x.lo, sw));
+      const long long Iy = __float2ll_rn(ldexpf(v[u].y.hi, sw)) + __float2ll_rn(ldexpf(v[u].y.lo, sw));
+      float dx[T], dy[T];
+      oz_digits<T>(Ix, dx);
+      oz_digits<T>(Iy, dy);
+#pragma unroll
+      for (int t = 0; t < T; ++t) put_bf16x2(dig + t * plane + (size_t)r * kpad + 2 * e, dx[t], dy[t]);
+    }
   }
 }
 
@@ -489,7 +534,9 @@ void run_gemm(const OzMat &A, const OzMat &B, int K, OzArgs p, double *work, siz
   p.groupA = EPI == OZ_GRAM ? p.tilesA : std::min(p.tilesA, 16);
   const CUtensorMap mA = digit_map(A.dig, K, A.rows, A.kpad, A.plane, OZ_M, T);
   const CUtensorMap mB = digit_map(B.dig, K, B.rows, B.kpad, B.plane, OZ_NB, T);
-  launch(EPI == OZ_GRAM ? "gram" : "lincomb", 64, k_oz_gemm<T, EPI>, dim3(tiles, 1, nsplit), dim3(OZ_THREADS), oz_smem<T>(), st, mA, mB, p);
+  p.nsplit = nsplit;
+  const int grid = std::min(tiles * nsplit, nsm);  // persistent: one CTA per SM
+  launch(EPI == OZ_GRAM ? "gram" : "lincomb", 64, k_oz_gemm<T, EPI>, dim3(grid), dim3(OZ_THREADS), oz_smem<T>(), st, mA, mB, p);
   WDF_CUDA_TRY(cudaGetLastError());
   if (EPI == OZ_GRAM && nsplit > 1) {
     launch("gram_sum", 0, k_oz_sum_splits, dim3((unsigned)(((size_t)A.rows * B.rows + 255) / 256)), dim3(256), 0, st, (const double *)work,
