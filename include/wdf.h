@@ -105,6 +105,12 @@ typedef struct wdf_options {
   int device;        /* CUDA device ordinal (default 0) */
   int warm_start;    /* WDF_PRECOND_LEARNED: start each solve from the model's first iterate
                         x0 = o1(v, G) K b instead of 0 (default 0) */
+  int residual_update; /* WDF_MIXED, WDF_MIXED_DF: after a batch's first full residual, take the
+                        residual of x + d as r - A d with A d in FP32 and its error bound
+                        eps_A ||d|| added to the stopping test, while that bound stays below
+                        cg_tol ||b|| / 10 (eps_A: 16 x the batch's largest measured
+                        ||A x - A_32 x|| / ||x||); 0 (default): every refinement recomputes
+                        b - A x in the residual precision */
 } wdf_options;
 
 /* Statistics of the last apply / Davidson call. */
@@ -159,6 +165,9 @@ int wdf_get_orbitals(wdf_ctx *ctx, double *eps, double *psi, int mem);
 /* Apply H (Eq. (1): kinetic + local + Kleinman-Bylander) to nvec half-sphere vectors.
  * in, out: [nvec][npw_h] complex, host or device per mem; out may alias in. */
 int wdf_apply_hamiltonian(wdf_ctx *ctx, int nvec, const double *in, double *out, int mem);
+
+/* Switch wdf_options.residual_update of a live context (0 or 1). Errors: WDF_EINVAL. */
+int wdf_set_residual_update(wdf_ctx *ctx, int on);
 
 /* Apply the operator of the Sternheimer equations of Sec. 2.1, A_v = H - eps_v + alpha P (P the
  * projector on the occupied space, alpha the shift of wdf_options), to nvec half-sphere vectors,

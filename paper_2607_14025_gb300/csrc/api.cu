@@ -491,6 +491,12 @@ int wdf_apply_hamiltonian(wdf_ctx *c, int nvec, const double *in, double *out, i
   });
 }
 
+int wdf_set_residual_update(wdf_ctx *c, int on) {
+  if (!c || (on != 0 && on != 1)) return WDF_EINVAL;
+  c->opt.residual_update = on;
+  return WDF_OK;
+}
+
 int wdf_apply_sternheimer_operator(wdf_ctx *c, int nvec, const int32_t *vidx, const double *in, double *out, int mem) {
   if (!c) return WDF_EINVAL;
   return guarded(c, [&] {

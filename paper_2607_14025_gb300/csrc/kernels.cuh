@@ -131,6 +131,8 @@ template <typename T>
 void launch_dot_partial(const Geo &g, const cplx<T> *A, const cplx<T> *B, int nvec, double *part, int nchunk,
                         cudaStream_t st);
 int dot_chunks(const Geo &g);
+// part[s * nchunk + c] = sum over chunk c of w_e |A_s[e] - B_s[e]|^2 (A FP64, B FP32)
+void launch_diff_partial(const Geo &g, const cplx<double> *A, const cplx<float> *B, int nvec, double *part, int nchunk, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------
 // CG state per solve (device arrays of length n unless noted)

@@ -521,6 +521,29 @@ void launch_dot_partial(const Geo &g, const cplx<T> *A, const cplx<T> *B, int nv
   WDF_CUDA_TRY(cudaGetLastError());
 }
 
+// per-vector partial sums of sum_e w_e |A_e - B_e|^2 with A in FP64 and B in FP32 (the deviation
+// of an FP32 result from an FP64-class one), in the chunks of k_dot_partial
+__global__ void __launch_bounds__(256) k_diff_partial(Geo g, const cplx<double> *__restrict__ A, const cplx<float> *__restrict__ B,
+                                                     double *__restrict__ part, int nchunk) {
+  const int s = blockIdx.x, c = blockIdx.y;
+  const int e0 = c * DCHUNK, e1 = min(g.nint, e0 + DCHUNK);
+  const cplx<double> *a = A + (size_t)s * g.ld;
+  const cplx<float> *b = B + (size_t)s * g.ld;
+  double v = 0.0;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const double dx = a[e].x - (double)b[e].x, dy = a[e].y - (double)b[e].y;
+    v += wgt(e, g.len0) * (dx * dx + dy * dy);
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0) part[(size_t)s * nchunk + c] = v;
+}
+
+void launch_diff_partial(const Geo &g, const cplx<double> *A, const cplx<float> *B, int nvec, double *part, int nchunk, cudaStream_t st) {
+  if (nvec <= 0) return;
+  launch("dot_partial", 64, k_diff_partial, dim3(dim3(nvec, nchunk)), dim3(256), 0, st, g, A, B, part, nchunk);
+  WDF_CUDA_TRY(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------------------------
 // conjugate gradients
 

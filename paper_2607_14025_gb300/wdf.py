@@ -72,6 +72,7 @@ class _Options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int),
         ("warm_start", ctypes.c_int),
+        ("residual_update", ctypes.c_int),
     ]
 
 
@@ -142,6 +143,7 @@ def load(path: str = LIB_PATH):
         "wdf_apply_hamiltonian": (I, [P, I, P, P, I]),
         "wdf_sternheimer": (I, [P, I, P, P, P, I, P]),
         "wdf_apply_sternheimer_operator": (I, [P, I, P, P, P, I]),
+        "wdf_set_residual_update": (I, [P, I]),
         "wdf_apply_chi0": (I, [P, I, P, P, P, I, P]),
         "wdf_pdep_davidson": (I, [P, I, I, I, D, I, P, P, P, I, P]),
         "wdf_apply_hamiltonian_noalloc": (I, [P, I, P, P]),
@@ -252,7 +254,7 @@ class Context:
     def __init__(self, system, psi=None, eps=None, precision: str = "mixed", precond: str = "tpa", cg_tol: float = 1e-8,
                  cg_maxiter: int = 1000, inner_tol: float = 1e-5, alpha: float = 0.0, max_batch: int = 0,
                  gs_tol: float = 1e-10, gs_maxiter: int = 300, gs_extra: int = 8, stream: Optional[int] = None,
-                 device: int = 0, data_on_device: bool = False, warm_start: bool = False):
+                 device: int = 0, data_on_device: bool = False, warm_start: bool = False, residual_update: bool = False):
         self._lib = load()
         self._ctx = ctypes.c_void_p()
         opt = _Options()
@@ -264,6 +266,7 @@ class Context:
         opt.stream = stream
         opt.device = device
         opt.warm_start = 1 if warm_start else 0
+        opt.residual_update = 1 if residual_update else 0
         keep: list = []
         s = _System()
         s.cell[:] = [float(v) for v in np.asarray(system.cell, dtype=np.float64).reshape(9)]
@@ -380,6 +383,10 @@ class Context:
     def set_wait_limit(self, polls: int):
         """Polls of the software device waits before they give up (wdf_set_wait_limit; 0: default)."""
         self._check(self._lib.wdf_set_wait_limit(self._ctx, int(polls)))
+
+    def set_residual_update(self, on: bool):
+        """Switch the bounded residual updates of the FP32 inner forms (wdf_options.residual_update)."""
+        self._check(self._lib.wdf_set_residual_update(self._ctx, 1 if on else 0))
 
     def apply_sternheimer_operator(self, vidx, x):
         """(H - eps_v + alpha P) x, vector k with v = vidx[k], in the residuals' precision."""
