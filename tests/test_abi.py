@@ -66,6 +66,7 @@ def test_strerror_and_defaults(lib):
     lib.wdf_default_options(ctypes.byref(o))
     assert o.precision == wdf.WDF_MIXED and o.precond == wdf.WDF_PRECOND_TPA
     assert o.cg_tol == 1e-8 and o.cg_maxiter == 1000 and o.inner_tol == 1e-5 and o.warm_start == 0
+    assert o.residual_update == 0  # every refinement recomputes b - A x unless asked
     t = wdf.TrainOpts()
     lib.wdf_default_train_opts(ctypes.byref(t))
     assert t.steps == 600 and t.lr == 3e-3 and t.npert == 8 and t.seed == 0
@@ -82,6 +83,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.wdf_set_model(None, None) == wdf.WDF_EINVAL
     assert lib.wdf_model_create(0, 0, None) == wdf.WDF_EINVAL
     assert lib.wdf_plane_variant(None, 32, None) == wdf.WDF_EINVAL
+    assert lib.wdf_apply_sternheimer_operator(None, 1, None, None, None, 0) == wdf.WDF_EINVAL
+    assert lib.wdf_set_residual_update(None, 1) == wdf.WDF_EINVAL
     lib.wdf_model_free(None)  # ignored
 
 
