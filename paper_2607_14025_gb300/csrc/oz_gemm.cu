@@ -25,12 +25,13 @@
 // accumulator block per group, T MMAs per 16 K values, T x 32 TMEM columns per chain; two chains
 // alternate between the two halves of a 512-column allocation.
 //
-// Kernel roles (384 threads, one CTA per SM): warp 0 one thread loads the T A planes and the T B
-// planes of a stage (32 K values) with tensor-memory-access copies; warp 1 one thread issues the
-// MMAs; warps 4-11 move every finished chain out of TMEM (warp w: TMEM lanes 32 (w mod 4) ..,
-// columns 16 ((w - 4) / 4) .. of each 32-column block) and write the result at the end. Every
-// mbarrier wait is bounded: on expiry the kernel raises the error flag, waits (bounded) for what
-// it issued, frees its TMEM and returns.
+// Kernel roles (384 threads, one persistent CTA per SM walking the work items = tiles x K splits):
+// warp 0 one thread loads the T A planes and the T B planes of a stage (32 K values) with
+// tensor-memory-access copies; warp 1 one thread issues the MMAs; warps 4-11 move every finished
+// chain out of TMEM (warp w: TMEM lanes 32 (w mod 4) .., columns 16 ((w - 4) / 4) .. of each
+// 32-column block) and write each item's result after its last chain, while the MMAs of the next
+// item fill the other TMEM half. Every mbarrier wait is bounded: on expiry the kernel raises the
+// error flag, waits (bounded) for what it issued, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
